@@ -1,0 +1,268 @@
+"""Python handle on the CPU oracle (oracle.cpp).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and bench.py's
+cpu_baseline / reference leg, never by the product package.
+
+Arrays are numpy float64 in the oracle's natural per-cell layout: y[cell, i] with
+y = [T, n_1, ..., n_{Ns-1}] (n in kmol per kg of mixture), Jacobians J[cell, i, j] = df_i/dy_j.
+Conversion between mass fractions and the state vector is done here in numpy (n_k = Y_k / W_k,
+and Y_Ns = 1 - sum of the others), independently of the CUDA path's own conversion kernel.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "oracle.cpp")
+LIB = os.path.join(HERE, "_build", "liboracle.so")
+
+OK, MAX_STEPS, H_UNDERFLOW, NONFINITE, SKIPPED = 0, 1, 2, 3, 4
+
+_lib = None
+_lock = threading.Lock()
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with g++ (plain -O2, no fast-math, no FP contraction)."""
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC",
+                               "-pthread", SRC, "-o", tmp])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            vp = C.c_void_p
+            lib.orc_last_error.restype = C.c_char_p
+            lib.orc_load.restype = vp
+            lib.orc_load.argtypes = [C.c_char_p]
+            lib.orc_free.argtypes = [vp]
+            lib.orc_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+            lib.orc_species.argtypes = [vp, _dp, _ip, _dp, _dp, _dp]
+            lib.orc_reactions.argtypes = [vp, _ip, _dp, _ip, _ip]
+            lib.orc_thermo.argtypes = [vp, C.c_int, C.c_double] + [C.POINTER(C.c_double)] * 3
+            lib.orc_thermo_cplx.argtypes = [vp, C.c_int, C.c_double, C.c_double, _dp]
+            lib.orc_source.argtypes = [vp, C.c_int, _dp, _dp, vp, _dp]
+            lib.orc_source_cplx.argtypes = [vp, _dp, vp, C.c_double, vp, vp, _dp, _dp]
+            lib.orc_jacobian.argtypes = [vp, C.c_int, _dp, _dp, vp, _dp, C.c_int]
+            lib.orc_rates.argtypes = [vp, _dp, C.c_double, vp] + [_dp] * 6
+            lib.orc_tableau.argtypes = [_dp]
+            lib.orc_step_linear.argtypes = [C.c_int, _dp, _dp, C.c_double, _dp, _dp]
+            lib.orc_integrate_linear.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_double,
+                                                 C.c_double, C.POINTER(C.c_int)]
+            lib.orc_step.argtypes = [vp, _dp, C.c_double, vp, C.c_double, _dp, _dp]
+            lib.orc_integrate.argtypes = [vp, C.c_int, _dp, _dp, vp, C.c_double, C.c_double,
+                                          C.c_double, vp, vp, vp, vp, vp, C.c_int, C.c_double,
+                                          C.c_double, C.c_int, C.c_int]
+            lib.orc_integrate_log.argtypes = [vp, _dp, C.c_double, vp, C.c_double, C.c_double,
+                                              C.c_double, C.c_double, C.c_int, _dp, C.c_int,
+                                              C.POINTER(C.c_int), C.POINTER(C.c_double)]
+            lib.orc_replay_cplx.argtypes = [vp, _dp, _dp, C.c_double, vp, vp, _dp, C.c_int]
+            lib.orc_replay.argtypes = [vp, _dp, C.c_double, vp, _dp, C.c_int]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def tableau() -> dict:
+    out = np.zeros(41)
+    _load().orc_tableau(out)
+    return {"gamma": out[0], "a": out[1:17].reshape(4, 4), "c": out[17:33].reshape(4, 4),
+            "m": out[33:37], "e": out[37:41]}
+
+
+def step_linear(A, y, h):
+    A = _f64(A)
+    y = _f64(y)
+    ynew = np.zeros_like(y)
+    err = np.zeros_like(y)
+    _load().orc_step_linear(len(y), A, y, h, ynew, err)
+    return ynew, err
+
+
+def integrate_linear(A, y, dt, rtol, atol):
+    A = _f64(A)
+    y = _f64(y).copy()
+    att = C.c_int(0)
+    st = _load().orc_integrate_linear(len(y), A, y, dt, rtol, atol, C.byref(att))
+    return y, st, att.value
+
+
+class Mechanism:
+    """An oracle-side parsed mechanism (oracle.cpp's own spec reader)."""
+
+    def __init__(self, path: str):
+        lib = _load()
+        self._lib = lib
+        h = lib.orc_load(path.encode())
+        if not h:
+            raise RuntimeError(lib.orc_last_error().decode())
+        self._h = h
+        ns, nr, ne = C.c_int(), C.c_int(), C.c_int()
+        lib.orc_info(h, C.byref(ns), C.byref(nr), C.byref(ne))
+        self.ns, self.nr, self.ne = ns.value, nr.value, ne.value
+        self.N = self.ns
+        self.W = np.zeros(self.ns)
+        self.elem = np.zeros(self.ne * self.ns, dtype=np.int32)
+        self.Tmid = np.zeros(self.ns)
+        self.hf_R = np.zeros(self.ns)
+        self.s_R = np.zeros(self.ns)
+        lib.orc_species(h, self.W, self.elem, self.Tmid, self.hf_R, self.s_R)
+        self.elem = self.elem.reshape(self.ne, self.ns)
+        self.kind = np.zeros(self.nr, dtype=np.int32)
+        self.lnA = np.zeros(self.nr)
+        nuf = np.zeros(self.nr * self.ns, dtype=np.int32)
+        nur = np.zeros(self.nr * self.ns, dtype=np.int32)
+        lib.orc_reactions(h, self.kind, self.lnA, nuf, nur)
+        self.nu_f = nuf.reshape(self.nr, self.ns)
+        self.nu_r = nur.reshape(self.nr, self.ns)
+
+    def __del__(self):
+        try:
+            self._lib.orc_free(self._h)
+        except Exception:
+            pass
+
+    # --------------------------------------------------------------------- conversions
+    def state_from_TY(self, T, Y):
+        """y = [T, Y_1/W_1, ..., Y_{Ns-1}/W_{Ns-1}] per cell (unit-mass basis)."""
+        T = np.atleast_1d(np.asarray(T, dtype=np.float64))
+        Y = np.atleast_2d(np.asarray(Y, dtype=np.float64))
+        y = np.empty((len(T), self.ns))
+        y[:, 0] = T
+        y[:, 1:] = Y[:, :-1] / self.W[:-1]
+        return y
+
+    def TY_from_state(self, y):
+        y = np.atleast_2d(y)
+        Y = np.empty((y.shape[0], self.ns))
+        Y[:, :-1] = y[:, 1:] * self.W[:-1]
+        Y[:, -1] = 1.0 - Y[:, :-1].sum(axis=1)
+        return y[:, 0].copy(), Y
+
+    def moles_all(self, y):
+        """All Ns species moles per kg, the bath gas closed by mass conservation."""
+        y = np.atleast_2d(y)
+        n = np.empty((y.shape[0], self.ns))
+        n[:, :-1] = y[:, 1:]
+        n[:, -1] = (1.0 - (y[:, 1:] * self.W[:-1]).sum(axis=1)) / self.W[-1]
+        return n
+
+    # --------------------------------------------------------------------- evaluation
+    def thermo(self, k, T):
+        cp, h, s = C.c_double(), C.c_double(), C.c_double()
+        self._lib.orc_thermo(self._h, int(k), float(T), C.byref(cp), C.byref(h), C.byref(s))
+        return cp.value, h.value, s.value
+
+    def thermo_cplx(self, k, T):
+        out = np.zeros(6)
+        self._lib.orc_thermo_cplx(self._h, int(k), T.real, T.imag, out)
+        return out[0] + 1j * out[1], out[2] + 1j * out[3], out[4] + 1j * out[5]
+
+    def source(self, y, P, lnA=None):
+        y = _f64(np.atleast_2d(y))
+        P = _f64(np.broadcast_to(np.asarray(P, dtype=np.float64), (y.shape[0],)))
+        lnA = None if lnA is None else _f64(lnA)
+        f = np.zeros_like(y)
+        self._lib.orc_source(self._h, y.shape[0], y, P, _ptr(lnA), f)
+        return f
+
+    def source_cplx(self, y, P, lnA=None):
+        y = np.asarray(y, dtype=np.complex128)
+        yr, yi = _f64(y.real), _f64(y.imag)
+        fr = np.zeros(self.ns)
+        fi = np.zeros(self.ns)
+        if lnA is None:
+            lr = li = None
+        else:
+            lnA = np.asarray(lnA, dtype=np.complex128)
+            lr, li = _f64(lnA.real), _f64(lnA.imag)
+        self._lib.orc_source_cplx(self._h, yr, _ptr(yi), float(P), _ptr(lr), _ptr(li), fr, fi)
+        return fr + 1j * fi
+
+    def jacobian(self, y, P, lnA=None, threads: int = 1):
+        y = _f64(np.atleast_2d(y))
+        P = _f64(np.broadcast_to(np.asarray(P, dtype=np.float64), (y.shape[0],)))
+        lnA = None if lnA is None else _f64(lnA)
+        J = np.zeros((y.shape[0], self.ns, self.ns))
+        self._lib.orc_jacobian(self._h, y.shape[0], y, P, _ptr(lnA), J, threads)
+        return J
+
+    def rates(self, y, P, lnA=None):
+        y = _f64(y)
+        lnA = None if lnA is None else _f64(lnA)
+        kf, kr, qf, qr = (np.zeros(self.nr) for _ in range(4))
+        om, Cc = np.zeros(self.ns), np.zeros(self.ns)
+        self._lib.orc_rates(self._h, y, float(P), _ptr(lnA), kf, kr, qf, qr, om, Cc)
+        return {"kf": kf, "kr": kr, "qf": qf, "qr": qr, "omega": om, "C": Cc}
+
+    def step(self, y, P, h, lnA=None):
+        y = _f64(y)
+        lnA = None if lnA is None else _f64(lnA)
+        ynew, err = np.zeros_like(y), np.zeros_like(y)
+        self._lib.orc_step(self._h, y, float(P), _ptr(lnA), float(h), ynew, err)
+        return ynew, err
+
+    def integrate(self, y, P, dt, rtol=1e-6, atol=1e-10, h=None, lnA=None, max_steps=100000,
+                  h_min=1e-20, T_min=0.0, fixed_steps=0, threads=None):
+        """Integrate every cell over [0, dt]; returns (y, info dict)."""
+        y = _f64(np.atleast_2d(y)).copy()
+        n = y.shape[0]
+        P = _f64(np.broadcast_to(np.asarray(P, dtype=np.float64), (n,)))
+        hh = np.zeros(n) if h is None else _f64(np.broadcast_to(h, (n,))).copy()
+        st, att, acc, rej = (np.zeros(n, dtype=np.int32) for _ in range(4))
+        lnA = None if lnA is None else _f64(lnA)
+        threads = threads or os.cpu_count() or 1
+        self._lib.orc_integrate(self._h, n, y, P, _ptr(lnA), dt, rtol, atol, _ptr(hh), _ptr(st),
+                                _ptr(att), _ptr(acc), _ptr(rej), max_steps, h_min, T_min,
+                                fixed_steps, threads)
+        return y, {"h": hh, "status": st, "attempts": att, "accepted": acc, "rejected": rej}
+
+    def integrate_log(self, y, P, dt, rtol=1e-6, atol=1e-10, h0=0.0, lnA=None, max_steps=100000):
+        y = _f64(y).copy()
+        cap = max_steps + 1
+        hs = np.zeros(cap)
+        st, hout = C.c_int(), C.c_double()
+        lnA = None if lnA is None else _f64(lnA)
+        n = self._lib.orc_integrate_log(self._h, y, float(P), _ptr(lnA), dt, rtol, atol, h0,
+                                        max_steps, hs, cap, C.byref(st), C.byref(hout))
+        return y, hs[:n].copy(), st.value, hout.value
+
+    def replay(self, y, P, hs, lnA=None):
+        y = _f64(y).copy()
+        lnA = None if lnA is None else _f64(lnA)
+        self._lib.orc_replay(self._h, y, float(P), _ptr(lnA), _f64(hs), len(hs))
+        return y
+
+    def replay_cplx(self, y, P, hs, lnA=None):
+        y = np.asarray(y, dtype=np.complex128)
+        yr, yi = _f64(y.real).copy(), _f64(y.imag).copy()
+        if lnA is None:
+            lr = li = None
+        else:
+            lnA = np.asarray(lnA, dtype=np.complex128)
+            lr, li = _f64(lnA.real), _f64(lnA.imag)
+        self._lib.orc_replay_cplx(self._h, yr, yi, float(P), _ptr(lr), _ptr(li), _f64(hs),
+                                  len(hs))
+        return yr + 1j * yi
