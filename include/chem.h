@@ -1,0 +1,156 @@
+/* Batched ROS4 chemistry integrator for GB300 (sm_103a), FP64: the C ABI.
+ *
+ * The library integrates the stiff constant-pressure chemical-kinetic ODE of every cell of a
+ * CFD domain independently over one operator-split step, as in Curtis, Niemeyer & Sung,
+ * "Accelerating reactive-flow simulations using vectorized chemistry integration":
+ *   - state of a cell: y = [T, n_1, ..., n_{Ns-1}], the last species (bath gas) closed
+ *     implicitly (Sec. 2.1, Eq. e:state_vec and Eq. e:n_nsp); here on a unit-mass basis, n_k in
+ *     kmol per kg of mixture, n_Ns = (1 - sum_k W_k n_k) / W_Ns, V = n_tot R T / P;
+ *   - source terms dy/dt = f(y) (Sec. 2.1, Eq. e:dphidt) and the analytical Jacobian
+ *     J = df/dy (Eq. e:jac), from Arrhenius, third-body, Lindemann and Troe rate constants
+ *     with reverse rates from NASA-7 equilibrium constants;
+ *   - a four-stage linearly implicit Rosenbrock method (ROS4, Hairer-Wanner coefficients) in
+ *     the transformed form of Sec. 2.3 (Eq. e:ros and below), with an embedded error estimate
+ *     and adaptive step size; the whole domain goes in one batched call that returns the
+ *     updated states and the last internal step size of each cell for reuse on the next
+ *     split step (Sec. 2.4.1, BatchedChemistryModel).
+ *
+ * Conventions for every entry point:
+ *   - SI units: T [K], P [Pa], dt and h [s], n [kmol/kg], f [K/s and kmol/kg/s].
+ *   - Per-cell arrays are FP64, cell-fastest ("structure of arrays"): component i of cell c
+ *     is at ptr[i * ld + c], with ld >= n_cells the leading dimension.  T, P, h, status are
+ *     plain [n_cells] vectors.
+ *   - Array pointers are DEVICE pointers owned by the caller (e.g. torch tensors), except in
+ *     chem_integrate_host.  The library owns mechanism handles and compiled modules.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream) and
+ *     return once the work is enqueued.  chem_integrate in CHEM_MODE_PERSISTENT does no host
+ *     synchronisation and no allocation, so it can be captured in a CUDA graph.
+ *   - Return value: 0 on success, negative on an argument, CUDA or NVRTC error; the message is
+ *     in chem_last_error() (thread-local).  Integration failures of single cells are never
+ *     errors: they are reported per cell in `status`.
+ */
+#ifndef CHEM_H
+#define CHEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chem_mech* chem_mech_t;
+
+/* error codes */
+#define CHEM_OK 0
+#define CHEM_EARG (-1)   /* invalid argument */
+#define CHEM_ECUDA (-2)  /* CUDA driver/runtime error */
+#define CHEM_ENVRTC (-3) /* run-time compilation failed */
+#define CHEM_EIO (-4)    /* spec file unreadable or malformed */
+#define CHEM_EWS (-5)    /* workspace too small */
+
+/* per-cell integration status (same codes as the CPU oracle) */
+#define CHEM_STATUS_OK 0
+#define CHEM_STATUS_MAX_STEPS 1   /* max_steps attempts used before reaching dt */
+#define CHEM_STATUS_H_UNDERFLOW 2 /* step size fell below h_min */
+#define CHEM_STATUS_NONFINITE 3   /* non-finite input state; cell left unchanged */
+#define CHEM_STATUS_SKIPPED 4     /* T < T_min: cell left unchanged (paper's reacting cut-off) */
+
+/* integration drivers */
+#define CHEM_MODE_PERSISTENT 0 /* one persistent launch, device work queue, per-team refill */
+#define CHEM_MODE_PLAIN 1      /* one launch per ROS4 step attempt over all cells, host polling */
+
+/* Options for chem_mech_load (NULL = defaults). */
+typedef struct {
+  int32_t team;        /* lanes per cell for the default kernel config: 1, 32, 64, 128, 256;
+                          0 = chosen from the mechanism size */
+  int32_t block;       /* threads per block; 0 = chosen with team */
+  int32_t verbose;     /* print compile logs (register use) to stderr */
+  const char* cache_dir; /* directory for compiled cubins; NULL = no disk cache */
+} chem_build_opts;
+
+/* Options for chem_integrate (NULL = defaults shown). */
+typedef struct {
+  int32_t max_steps;   /* attempts (accepted + rejected) per cell and call; default 100000 */
+  double h_min;        /* smallest step size [s] before CHEM_STATUS_H_UNDERFLOW; 1e-20 */
+  double T_min;        /* cells with T < T_min are skipped; 0 = none */
+  int32_t mode;        /* CHEM_MODE_PERSISTENT (default) or CHEM_MODE_PLAIN */
+  int32_t team;        /* kernel config override (0 = mechanism default) */
+  int32_t block;
+  const double* lnA;   /* device [Nr]: ln of the pre-exponential factors (SI units; for falloff
+                          reactions the high-pressure limit); NULL = the mechanism's values */
+  int32_t* attempts;   /* device [n_cells] out: step attempts per cell; NULL = not written */
+} chem_int_opts;
+
+/* Parse a mechanism spec file (format: paper_2205_05681_gb300/synth.py docstring), build its
+ * tables, generate its specialised CUDA source and compile it for sm_103a with NVRTC (or load
+ * the cubin from cache_dir).  Host-side; needs a current CUDA device to load the module.
+ * out receives the handle.  Errors: CHEM_EIO, CHEM_ENVRTC, CHEM_ECUDA. */
+int chem_mech_load(const char* spec_path, const chem_build_opts* opts, chem_mech_t* out);
+
+/* As chem_mech_load but only generates and compiles the source (no CUDA device needed); used
+ * by the build step to check that every mechanism compiles.  Writes ptxas' register report
+ * into log (capacity log_cap bytes, NUL-terminated) when log != NULL. */
+int chem_mech_compile_only(const char* spec_path, const chem_build_opts* opts, char* log,
+                           size_t log_cap);
+
+/* Release a mechanism and its modules. */
+int chem_mech_free(chem_mech_t mech);
+
+/* Sizes of a mechanism: species (= state length N), reactions, elements. */
+int chem_mech_info(chem_mech_t mech, int32_t* n_species, int32_t* n_reactions,
+                   int32_t* n_elements);
+
+/* Built-in ln A of every reaction (SI) copied to host array lnA[Nr]. */
+int chem_mech_lnA(chem_mech_t mech, double* lnA);
+
+/* Source terms f(y) (Eq. e:dphidt) for n_cells cells.
+ *   T [n_cells], P [n_cells], n [(Ns-1) x ld] species moles (state entries 1..Ns-1),
+ *   f [Ns x ld] out: f[0] = dT/dt, f[1+k] = dn_k/dt.  lnA: device [Nr] or NULL. */
+int chem_eval_source(chem_mech_t mech, int64_t n_cells, const double* T, const double* P,
+                     const double* n, double* f, int64_t ld, const double* lnA, void* stream);
+
+/* Analytical Jacobian J = df/dy (Eq. e:jac) on y = [T, n_1..n_{Ns-1}].
+ *   J [(Ns*Ns) x ld] out: entry (i, j) of cell c at J[(i*Ns + j) * ld + c] (row-major within
+ *   a cell).  Other arguments as chem_eval_source. */
+int chem_eval_jacobian(chem_mech_t mech, int64_t n_cells, const double* T, const double* P,
+                       const double* n, double* J, int64_t ld, const double* lnA,
+                       void* stream);
+
+/* Bytes of device workspace chem_integrate needs for n_cells cells with these options. */
+size_t chem_integrate_workspace(chem_mech_t mech, int64_t n_cells, const chem_int_opts* opts);
+
+/* Integrate every cell from t = 0 to t = dt in place (Sec. 2.3 ROS4, Sec. 2.4.1 batching).
+ *   T [n_cells] in/out, P [n_cells] in (constant during the step), Y [Ns x ld] mass fractions
+ *   in/out (all Ns species; the bath gas is written from the closure).
+ *   h [n_cells] in/out (nullable): in, the first step size to try (<= 0 means dt); out, the
+ *   step size proposed for the next call.  status [n_cells] out (nullable).
+ *   rtol, atol: the error tolerances of the weighted RMS error norm.
+ *   workspace: device memory of chem_integrate_workspace() bytes, caller-owned, 256-byte
+ *   aligned; its content need not be preserved between calls. */
+int chem_integrate(chem_mech_t mech, int64_t n_cells, double* T, const double* P, double* Y,
+                   int64_t ld, double dt, double rtol, double atol, double* h, int32_t* status,
+                   const chem_int_opts* opts, void* workspace, size_t ws_bytes, void* stream);
+
+/* chem_integrate on HOST arrays (ld = n_cells): copies T, P, Y, h to the device, integrates
+ * with the persistent driver and copies T, Y, h, status back, all on `stream`, and waits for
+ * completion.  Device buffers are allocated by the library on first use and reused.  h and
+ * status may be NULL.  This is the end-to-end entry point for callers whose data lives on the
+ * host. */
+int chem_integrate_host(chem_mech_t mech, int64_t n_cells, double* T, const double* P,
+                        double* Y, double dt, double rtol, double atol, double* h,
+                        int32_t* status, const chem_int_opts* opts, void* stream);
+
+/* Kernel configuration actually used by chem_integrate for these options (team, block,
+ * dynamic shared memory bytes, registers per thread); for reports. */
+int chem_kernel_config(chem_mech_t mech, const chem_int_opts* opts, int32_t* team,
+                       int32_t* block, int32_t* smem_bytes, int32_t* regs);
+
+/* Message of the last failed call on this thread. */
+const char* chem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEM_H */

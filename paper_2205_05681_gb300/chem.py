@@ -1,0 +1,232 @@
+"""Thin Python binding of the C ABI in include/chem.h (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; this module only passes device pointers
+of torch tensors (FP64, cell-fastest [component, cell] layout), sizes and the current CUDA
+stream.  It raises if the compiled library is missing: there is no CPU fallback.
+
+Names follow the C ABI without the ``chem_`` prefix: mech_load, eval_source, eval_jacobian,
+integrate, integrate_workspace, integrate_host, kernel_config.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+from . import build as _build
+
+MODE_PERSISTENT = 0
+MODE_PLAIN = 1
+STATUS_OK, STATUS_MAX_STEPS, STATUS_H_UNDERFLOW, STATUS_NONFINITE, STATUS_SKIPPED = 0, 1, 2, 3, 4
+
+EXPORTS = ["chem_mech_load", "chem_mech_compile_only", "chem_mech_free", "chem_mech_info",
+           "chem_mech_lnA", "chem_eval_source", "chem_eval_jacobian", "chem_integrate_workspace",
+           "chem_integrate", "chem_integrate_host", "chem_kernel_config", "chem_last_error"]
+
+CACHE_DIR = os.environ.get("CHEM_CACHE_DIR", os.path.join(os.path.dirname(__file__), "_cache"))
+
+
+class BuildOpts(C.Structure):
+    _fields_ = [("team", C.c_int32), ("block", C.c_int32), ("verbose", C.c_int32),
+                ("cache_dir", C.c_char_p)]
+
+
+class IntOpts(C.Structure):
+    _fields_ = [("max_steps", C.c_int32), ("h_min", C.c_double), ("T_min", C.c_double),
+                ("mode", C.c_int32), ("team", C.c_int32), ("block", C.c_int32),
+                ("lnA", C.c_void_p), ("attempts", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+class ChemError(RuntimeError):
+    pass
+
+
+def library(build_if_missing: bool = True):
+    """Load libchem.so (building it in-tree first if asked)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise ChemError("libchem.so is not built (run paper_2205_05681_gb300/build.py)")
+            lib = C.CDLL(path)
+            vp, i64, dbl = C.c_void_p, C.c_int64, C.c_double
+            lib.chem_last_error.restype = C.c_char_p
+            lib.chem_mech_load.argtypes = [C.c_char_p, C.POINTER(BuildOpts), C.POINTER(vp)]
+            lib.chem_mech_compile_only.argtypes = [C.c_char_p, C.POINTER(BuildOpts), C.c_char_p,
+                                                   C.c_size_t]
+            lib.chem_mech_free.argtypes = [vp]
+            lib.chem_mech_info.argtypes = [vp] + [C.POINTER(C.c_int32)] * 3
+            lib.chem_mech_lnA.argtypes = [vp, vp]
+            lib.chem_eval_source.argtypes = [vp, i64, vp, vp, vp, vp, i64, vp, vp]
+            lib.chem_eval_jacobian.argtypes = [vp, i64, vp, vp, vp, vp, i64, vp, vp]
+            lib.chem_integrate_workspace.restype = C.c_size_t
+            lib.chem_integrate_workspace.argtypes = [vp, i64, C.POINTER(IntOpts)]
+            lib.chem_integrate.argtypes = [vp, i64, vp, vp, vp, i64, dbl, dbl, dbl, vp, vp,
+                                           C.POINTER(IntOpts), vp, C.c_size_t, vp]
+            lib.chem_integrate_host.argtypes = [vp, i64, vp, vp, vp, dbl, dbl, dbl, vp, vp,
+                                                C.POINTER(IntOpts), vp]
+            lib.chem_kernel_config.argtypes = [vp, C.POINTER(IntOpts)] + [C.POINTER(C.c_int32)] * 4
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise ChemError("chem error %d: %s" % (rc, library().chem_last_error().decode()))
+
+
+def compile_only(spec_path: str, team: int = 0, block: int = 0, cache_dir: Optional[str] = None,
+                 verbose: bool = False) -> str:
+    """Generate and NVRTC-compile a mechanism's kernels for sm_103a (no GPU needed)."""
+    buf = C.create_string_buffer(1 << 16)
+    o = BuildOpts(team, block, int(verbose), cache_dir.encode() if cache_dir else None)
+    _check(library().chem_mech_compile_only(spec_path.encode(), C.byref(o), buf, len(buf)))
+    return buf.value.decode(errors="replace")
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _req(t, name, dtype=None, shape=None):
+    import torch
+    dtype = dtype or torch.float64
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ChemError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ChemError("%s must be %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ChemError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ChemError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+    return t
+
+
+class Mechanism:
+    """A loaded mechanism: tables on the host, compiled sm_103a kernels on the current device."""
+
+    def __init__(self, spec_path: str, team: int = 0, block: int = 0, verbose: bool = False,
+                 cache_dir: Optional[str] = CACHE_DIR):
+        lib = library()
+        if cache_dir:
+            os.makedirs(cache_dir, exist_ok=True)
+        self._lib = lib
+        self.spec_path = spec_path
+        h = C.c_void_p()
+        o = BuildOpts(team, block, int(verbose), cache_dir.encode() if cache_dir else None)
+        _check(lib.chem_mech_load(spec_path.encode(), C.byref(o), C.byref(h)))
+        self._h = h
+        ns, nr, ne = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib.chem_mech_info(h, C.byref(ns), C.byref(nr), C.byref(ne)))
+        self.ns, self.nr, self.ne = ns.value, nr.value, ne.value
+        self.N = self.ns
+
+    def __del__(self):
+        try:
+            self._lib.chem_mech_free(self._h)
+        except Exception:
+            pass
+
+    def lnA(self):
+        import numpy as np
+        out = np.zeros(self.nr)
+        _check(self._lib.chem_mech_lnA(self._h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    # ------------------------------------------------------------------ evaluation
+    def eval_source(self, T, P, n, lnA=None, stream=None):
+        """T, P [C]; n [Ns-1, C] -> f [Ns, C] (f[0] = dT/dt)."""
+        import torch
+        Cn = T.shape[0]
+        _req(T, "T", shape=(Cn,)); _req(P, "P", shape=(Cn,)); _req(n, "n", shape=(self.ns - 1, Cn))
+        if lnA is not None:
+            _req(lnA, "lnA", shape=(self.nr,))
+        f = torch.empty((self.ns, Cn), dtype=torch.float64, device=T.device)
+        _check(self._lib.chem_eval_source(self._h, Cn, _ptr(T), _ptr(P), _ptr(n), _ptr(f), Cn,
+                                          _ptr(lnA), _stream(stream)))
+        return f
+
+    def eval_jacobian(self, T, P, n, lnA=None, stream=None):
+        """-> J [Ns*Ns, C], row-major within a cell."""
+        import torch
+        Cn = T.shape[0]
+        _req(T, "T", shape=(Cn,)); _req(P, "P", shape=(Cn,)); _req(n, "n", shape=(self.ns - 1, Cn))
+        if lnA is not None:
+            _req(lnA, "lnA", shape=(self.nr,))
+        J = torch.empty((self.ns * self.ns, Cn), dtype=torch.float64, device=T.device)
+        _check(self._lib.chem_eval_jacobian(self._h, Cn, _ptr(T), _ptr(P), _ptr(n), _ptr(J), Cn,
+                                            _ptr(lnA), _stream(stream)))
+        return J
+
+    # ------------------------------------------------------------------ integration
+    def opts(self, mode=MODE_PERSISTENT, max_steps=0, h_min=0.0, T_min=0.0, team=0, block=0,
+             lnA=None, attempts=None) -> IntOpts:
+        return IntOpts(max_steps, h_min, T_min, mode, team, block,
+                       None if lnA is None else lnA.data_ptr(),
+                       None if attempts is None else attempts.data_ptr())
+
+    def integrate_workspace(self, n_cells: int, opts: Optional[IntOpts] = None) -> int:
+        o = opts or self.opts()
+        return int(self._lib.chem_integrate_workspace(self._h, n_cells, C.byref(o)))
+
+    def workspace(self, n_cells: int, opts: Optional[IntOpts] = None, device="cuda"):
+        import torch
+        nbytes = self.integrate_workspace(n_cells, opts)
+        return torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=device)
+
+    def integrate(self, T, P, Y, dt, rtol=1e-6, atol=1e-10, h=None, status=None, opts=None,
+                  workspace=None, stream=None):
+        """In place: T [C], Y [Ns, C] (mass fractions); h [C] in/out (optional)."""
+        import torch
+        Cn = T.shape[0]
+        _req(T, "T", shape=(Cn,)); _req(P, "P", shape=(Cn,)); _req(Y, "Y", shape=(self.ns, Cn))
+        if h is not None:
+            _req(h, "h", shape=(Cn,))
+        if status is not None:
+            _req(status, "status", dtype=torch.int32, shape=(Cn,))
+        o = opts or self.opts()
+        if workspace is None:
+            workspace = self.workspace(Cn, o, device=T.device)
+        _check(self._lib.chem_integrate(self._h, Cn, _ptr(T), _ptr(P), _ptr(Y), Cn, dt, rtol,
+                                        atol, _ptr(h), _ptr(status), C.byref(o),
+                                        _ptr(workspace), workspace.numel(), _stream(stream)))
+        return T, Y
+
+    def integrate_host(self, T, P, Y, dt, rtol=1e-6, atol=1e-10, h=None, status=None,
+                       opts=None, stream=None):
+        """Numpy (host) arrays in place: T [C], P [C], Y [Ns, C] C-contiguous float64."""
+        import numpy as np
+        Cn = T.shape[0]
+        for a, nm in ((T, "T"), (P, "P"), (Y, "Y")):
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                raise ChemError("%s must be C-contiguous float64" % nm)
+        if Y.shape != (self.ns, Cn):
+            raise ChemError("Y must be [Ns, C]")
+        hp = None if h is None else h.ctypes.data_as(C.c_void_p)
+        sp = None if status is None else status.ctypes.data_as(C.c_void_p)
+        o = opts or self.opts()
+        _check(self._lib.chem_integrate_host(self._h, Cn, T.ctypes.data_as(C.c_void_p),
+                                             P.ctypes.data_as(C.c_void_p),
+                                             Y.ctypes.data_as(C.c_void_p), dt, rtol, atol, hp, sp,
+                                             C.byref(o), _stream(stream)))
+
+    def kernel_config(self, opts: Optional[IntOpts] = None):
+        o = opts or self.opts()
+        t, b, s, r = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(self._lib.chem_kernel_config(self._h, C.byref(o), C.byref(t), C.byref(b),
+                                            C.byref(s), C.byref(r)))
+        return {"team": t.value, "block": b.value, "smem": s.value, "regs": r.value}

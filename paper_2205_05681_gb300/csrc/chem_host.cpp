@@ -1,0 +1,844 @@
+// Host side of the batched ROS4 chemistry integrator: spec reader, mechanism compiler
+// (per-mechanism CUDA source -> NVRTC -> sm_103a cubin), module cache and the C ABI of
+// include/chem.h.  No torch types: callers pass device pointers and a cudaStream_t as void*.
+#include "chem.h"
+
+#include <cuda.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <functional>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "device_src.inc"  // const char* const kDeviceSource: ros4_device.cuh as a string
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[2048];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CU_TRY(call)                                                               \
+  do {                                                                             \
+    CUresult _r = (call);                                                          \
+    if (_r != CUDA_SUCCESS) {                                                      \
+      const char* _s = nullptr;                                                    \
+      drv::cuGetErrorString(_r, &_s);                                                   \
+      return fail(CHEM_ECUDA, "%s failed: %s", #call, _s ? _s : "unknown error"); \
+    }                                                                              \
+  } while (0)
+
+
+// ------------------------------------------------------------------------------ driver API
+// The CUDA driver library is opened at run time so that this library loads (and can compile
+// kernels with NVRTC) on machines without a GPU driver; any device call then fails cleanly.
+namespace drv {
+#define CHEM_STR2(x) #x
+#define CHEM_STR(x) CHEM_STR2(x)
+#define CHEM_DRV_FUNCS(X)                                                                       \
+  X(cuInit) X(cuGetErrorString) X(cuCtxGetCurrent) X(cuCtxSetCurrent) X(cuCtxGetDevice)          \
+  X(cuDeviceGet) X(cuDevicePrimaryCtxRetain) X(cuDeviceGetAttribute) X(cuModuleLoadData)        \
+  X(cuModuleUnload) X(cuModuleGetFunction) X(cuModuleGetGlobal) X(cuFuncSetAttribute)           \
+  X(cuFuncGetAttribute) X(cuOccupancyMaxActiveBlocksPerMultiprocessor) X(cuLaunchKernel)         \
+  X(cuMemsetD32Async) X(cuMemcpyDtoH) X(cuMemcpyDtoHAsync) X(cuMemcpyHtoDAsync)                 \
+  X(cuStreamSynchronize) X(cuMemHostAlloc) X(cuMemFreeHost) X(cuMemAlloc) X(cuMemFree)
+#define CHEM_DECL(fn) decltype(&::fn) fn = nullptr;
+CHEM_DRV_FUNCS(CHEM_DECL)
+#undef CHEM_DECL
+std::once_flag once;
+std::string load_error;
+
+bool load() {
+  std::call_once(once, [] {
+    void* h = dlopen("libcuda.so.1", RTLD_NOW | RTLD_LOCAL);
+    if (!h) {
+      load_error = std::string("cannot load the CUDA driver: ") + dlerror();
+      return;
+    }
+#define CHEM_LOAD(fn)                                                   \
+    fn = reinterpret_cast<decltype(fn)>(dlsym(h, CHEM_STR(fn)));        \
+    if (!fn && load_error.empty()) load_error = "missing driver symbol " CHEM_STR(fn);
+    CHEM_DRV_FUNCS(CHEM_LOAD)
+#undef CHEM_LOAD
+  });
+  return load_error.empty();
+}
+}  // namespace drv
+
+// ------------------------------------------------------------------------------ mechanism data
+
+constexpr int kMaxSide = 3;  // distinct species per reaction side
+
+struct SpeciesData {
+  std::string name;
+  double W = 0;
+  double Tmid = 1000;
+  double nasa[2][7] = {};  // [low, high][a1..a7]
+};
+
+struct ReactionData {
+  int kind = 0;  // 0 ELEM, 1 THIRD, 2 LIND, 3 TROE
+  int nre = 0, npr = 0;
+  int rsp[kMaxSide] = {}, rnu[kMaxSide] = {}, psp[kMaxSide] = {}, pnu[kMaxSide] = {};
+  double lnA = 0, b = 0, theta = 0;  // SI
+  std::vector<std::pair<int, double>> eff;  // non-default third-body efficiencies
+  double lnA0 = 0, b0 = 0, theta0 = 0;
+  double troe[4] = {};  // a, T***, T*, T**
+};
+
+struct MechData {
+  std::string name;
+  int n_elements = 0;
+  std::vector<SpeciesData> sp;
+  std::vector<ReactionData> rx;
+};
+
+// Spec reader (format documented in paper_2205_05681_gb300/synth.py).
+struct LineReader {
+  std::ifstream in;
+  int lineno = 0;
+  std::vector<std::string> tok;
+  bool next() {
+    std::string s;
+    while (std::getline(in, s)) {
+      ++lineno;
+      const size_t h = s.find('#');
+      if (h != std::string::npos) s.resize(h);
+      tok.clear();
+      std::istringstream ss(s);
+      std::string t;
+      while (ss >> t) tok.push_back(t);
+      if (!tok.empty()) return true;
+    }
+    return false;
+  }
+};
+
+bool to_double(const std::string& s, double* v) {
+  char* end = nullptr;
+  *v = std::strtod(s.c_str(), &end);
+  return end && *end == '\0';
+}
+bool to_int(const std::string& s, int* v) {
+  char* end = nullptr;
+  long x = std::strtol(s.c_str(), &end, 10);
+  *v = (int)x;
+  return end && *end == '\0';
+}
+
+constexpr double kRcal = 1.987204258640832;  // cal/(mol K)
+constexpr double kCgsToSi = 1e-3;            // cm^3/mol -> m^3/kmol
+
+int read_spec(const char* path, MechData* m) {
+  LineReader r;
+  r.in.open(path);
+  if (!r.in) return fail(CHEM_EIO, "cannot open spec file %s", path);
+  std::map<std::string, int> idx;
+  int want_sp = -1, want_rx = -1;
+  auto bad = [&](const char* what) { return fail(CHEM_EIO, "%s:%d: %s", path, r.lineno, what); };
+  auto side = [&](size_t& p, int* sp, int* nu, int* n) -> int {
+    int cnt;
+    if (p >= r.tok.size() || !to_int(r.tok[p++], &cnt) || cnt < 0 || cnt > kMaxSide) return -1;
+    *n = cnt;
+    for (int i = 0; i < cnt; ++i) {
+      if (p + 1 >= r.tok.size()) return -1;
+      auto it = idx.find(r.tok[p++]);
+      if (it == idx.end()) return -1;
+      sp[i] = it->second;
+      if (!to_int(r.tok[p++], &nu[i]) || nu[i] < 1 || nu[i] > 3) return -1;
+    }
+    return 0;
+  };
+  while (r.next()) {
+    const std::string& tag = r.tok[0];
+    if (tag == "MECHANISM") {
+      if (r.tok.size() > 1) m->name = r.tok[1];
+    } else if (tag == "ELEMENTS") {
+      m->n_elements = (int)r.tok.size() - 1;
+    } else if (tag == "SPECIES") {
+      if (r.tok.size() != 2 || !to_int(r.tok[1], &want_sp)) return bad("bad SPECIES line");
+    } else if (tag == "SP") {
+      const size_t need = 2 + 1 + m->n_elements + 5;
+      if (r.tok.size() != need) return bad("bad SP line");
+      SpeciesData s;
+      s.name = r.tok[1];
+      if (!to_double(r.tok[2], &s.W) || !(s.W > 0)) return bad("bad molecular weight");
+      if (!to_double(r.tok[3 + m->n_elements + 1], &s.Tmid)) return bad("bad Tmid");
+      idx[s.name] = (int)m->sp.size();
+      m->sp.push_back(s);
+    } else if (tag == "LO" || tag == "HI") {
+      if (m->sp.empty() || r.tok.size() != 8) return bad("bad NASA line");
+      double* a = m->sp.back().nasa[tag == "LO" ? 0 : 1];
+      for (int i = 0; i < 7; ++i)
+        if (!to_double(r.tok[1 + i], &a[i])) return bad("bad NASA coefficient");
+    } else if (tag == "REACTIONS") {
+      if (r.tok.size() != 2 || !to_int(r.tok[1], &want_rx)) return bad("bad REACTIONS line");
+    } else if (tag == "R") {
+      if (r.tok.size() < 2) return bad("bad R line");
+      ReactionData x;
+      const std::string& k = r.tok[1];
+      x.kind = k == "ELEM" ? 0 : k == "THIRD" ? 1 : k == "LIND" ? 2 : k == "TROE" ? 3 : -1;
+      if (x.kind < 0) return bad("unknown reaction type");
+      size_t p = 2;
+      if (side(p, x.rsp, x.rnu, &x.nre) || side(p, x.psp, x.pnu, &x.npr)) return bad("bad reaction side");
+      if (x.nre == 0 || x.npr == 0) return bad("empty reaction side");
+      double A, Ea;
+      if (p + 3 != r.tok.size() || !to_double(r.tok[p], &A) || !to_double(r.tok[p + 1], &x.b) ||
+          !to_double(r.tok[p + 2], &Ea) || !(A > 0))
+        return bad("bad Arrhenius data");
+      int order = (x.kind == 1) ? 1 : 0;
+      for (int i = 0; i < x.nre; ++i) order += x.rnu[i];
+      x.lnA = std::log(A) + (order - 1) * std::log(kCgsToSi);
+      x.theta = Ea / kRcal;
+      m->rx.push_back(x);
+    } else if (tag == "EFF") {
+      if (m->rx.empty()) return bad("EFF before R");
+      int cnt;
+      if (r.tok.size() < 2 || !to_int(r.tok[1], &cnt) || r.tok.size() != (size_t)(2 + 2 * cnt))
+        return bad("bad EFF line");
+      for (int i = 0; i < cnt; ++i) {
+        auto it = idx.find(r.tok[2 + 2 * i]);
+        double e;
+        if (it == idx.end() || !to_double(r.tok[3 + 2 * i], &e)) return bad("bad efficiency");
+        m->rx.back().eff.push_back({it->second, e});
+      }
+    } else if (tag == "LOW") {
+      if (m->rx.empty() || r.tok.size() != 4) return bad("bad LOW line");
+      ReactionData& x = m->rx.back();
+      double A0, Ea0;
+      if (!to_double(r.tok[1], &A0) || !to_double(r.tok[2], &x.b0) || !to_double(r.tok[3], &Ea0) || !(A0 > 0))
+        return bad("bad LOW data");
+      int order = 1;
+      for (int i = 0; i < x.nre; ++i) order += x.rnu[i];
+      x.lnA0 = std::log(A0) + (order - 1) * std::log(kCgsToSi);
+      x.theta0 = Ea0 / kRcal;
+    } else if (tag == "TROE") {
+      if (m->rx.empty() || r.tok.size() != 5) return bad("bad TROE line");
+      for (int i = 0; i < 4; ++i)
+        if (!to_double(r.tok[1 + i], &m->rx.back().troe[i])) return bad("bad TROE data");
+    } else if (tag == "END") {
+      break;
+    } else {
+      return bad("unknown record");
+    }
+  }
+  if ((int)m->sp.size() != want_sp || (int)m->rx.size() != want_rx)
+    return fail(CHEM_EIO, "%s: species/reaction counts do not match the declared counts", path);
+  if (m->sp.size() < 2) return fail(CHEM_EIO, "%s: need at least two species", path);
+  for (auto& x : m->rx) {
+    if (x.kind >= 2 && x.lnA0 == 0 && x.b0 == 0) return fail(CHEM_EIO, "%s: falloff reaction without LOW", path);
+    if (x.kind == 3 && !(x.troe[1] > 0 && x.troe[2] > 0)) return fail(CHEM_EIO, "%s: bad TROE temperatures", path);
+  }
+  return 0;
+}
+
+// ------------------------------------------------------------------------------ code generation
+
+// Hairer & Wanner L-stable ROS4 (Solving ODEs II, Sec. IV.7) in transformed variables: gamma,
+// a_ij, c_ij, m_i and error weights e_i.  Stage 4 uses the stage-3 argument (a_4j = a_3j).
+struct Ros4Coefficients {
+  double gamma = 0.57282;
+  double a21 = 2.0, a31 = 1.867943637803922, a32 = 0.2344449711399156;
+  double c21 = -7.137615036412310, c31 = 2.580708087951457, c32 = 0.6515950076447975;
+  double c41 = -2.137148994382534, c42 = -0.3214669691237626, c43 = -0.6949742501781779;
+  double m1 = 2.255570073418735, m2 = 0.2870493262186792, m3 = 0.4353179431840180, m4 = 1.093502252409163;
+  double e1 = -0.2815431932141155, e2 = -0.07276199124938920, e3 = -0.1082196201495311, e4 = -1.093502252409163;
+};
+
+std::string num(double v) {
+  char b[40];
+  snprintf(b, sizeof(b), "%.17g", v);
+  std::string s(b);
+  if (s.find_first_of(".eEn") == std::string::npos) s += ".0";
+  return s;
+}
+
+template <class F>
+void emit_array(std::ostringstream& o, const char* type, const char* name, const std::string& dims, int n, F f) {
+  o << "__device__ const " << type << " " << name << dims << " = {";
+  for (int i = 0; i < n; ++i) o << (i ? "," : "") << f(i);
+  o << "};\n";
+}
+
+std::string emit_mechanism(const MechData& m, int team, int tpb) {
+  const int ns = (int)m.sp.size(), nr = (int)m.rx.size();
+  std::ostringstream o;
+  o << "// generated for mechanism " << m.name << "\n";
+  o << "#define NS " << ns << "\n#define NR " << nr << "\n#define TEAM " << team << "\n#define TPB " << tpb
+    << "\n#define MAXP " << kMaxSide << "\n";
+  Ros4Coefficients c;
+  o << "#define RGAM " << num(c.gamma) << "\n#define RA21 " << num(c.a21) << "\n#define RA31 " << num(c.a31)
+    << "\n#define RA32 " << num(c.a32) << "\n#define RC21 " << num(c.c21) << "\n#define RC31 " << num(c.c31)
+    << "\n#define RC32 " << num(c.c32) << "\n#define RC41 " << num(c.c41) << "\n#define RC42 " << num(c.c42)
+    << "\n#define RC43 " << num(c.c43) << "\n#define RM1 " << num(c.m1) << "\n#define RM2 " << num(c.m2)
+    << "\n#define RM3 " << num(c.m3) << "\n#define RM4 " << num(c.m4) << "\n#define RE1 " << num(c.e1)
+    << "\n#define RE2 " << num(c.e2) << "\n#define RE3 " << num(c.e3) << "\n#define RE4 " << num(c.e4) << "\n";
+  const double Wb = m.sp[ns - 1].W;
+  emit_array(o, "double", "mk_W", "[" + std::to_string(ns) + "]", ns, [&](int k) { return num(m.sp[k].W); });
+  emit_array(o, "double", "mk_invW", "[" + std::to_string(ns) + "]", ns, [&](int k) { return num(1.0 / m.sp[k].W); });
+  emit_array(o, "double", "mk_wratio", "[" + std::to_string(std::max(ns - 1, 1)) + "]", ns - 1,
+             [&](int k) { return num(m.sp[k].W / Wb); });
+  emit_array(o, "double", "mk_Tmid", "[" + std::to_string(ns) + "]", ns, [&](int k) { return num(m.sp[k].Tmid); });
+  // NASA-7 with the divisions folded: cp/R (a1..a5), h/RT (a1, a2/2, a3/3, a4/4, a5/5, a6),
+  // s/R (a1 [x lnT], a2, a3/2, a4/3, a5/4, -, a7), dcp/dT/R (a2, 2a3, 3a4, 4a5)
+  auto nasa_table = [&](const char* name, int width, std::function<double(const double*, int)> f) {
+    o << "__device__ const double " << name << "[" << ns << "][2][" << width << "] = {";
+    for (int k = 0; k < ns; ++k) {
+      o << (k ? "," : "") << "{";
+      for (int r = 0; r < 2; ++r) {
+        o << (r ? "," : "") << "{";
+        for (int i = 0; i < width; ++i) o << (i ? "," : "") << num(f(m.sp[k].nasa[r], i));
+        o << "}";
+      }
+      o << "}";
+    }
+    o << "};\n";
+  };
+  nasa_table("mk_cp", 5, [](const double* a, int i) { return a[i]; });
+  nasa_table("mk_h", 6, [](const double* a, int i) { return i < 5 ? a[i] / (i + 1) : a[5]; });
+  nasa_table("mk_s", 7, [](const double* a, int i) {
+    if (i == 0) return a[0];
+    if (i < 5) return a[i] / i;
+    return i == 6 ? a[6] : 0.0;
+  });
+  nasa_table("mk_dcp", 4, [](const double* a, int i) { return a[i + 1] * (i + 1); });
+  const std::string R = "[" + std::to_string(nr) + "]";
+  const std::string RP = "[" + std::to_string(nr) + "][" + std::to_string(kMaxSide) + "]";
+  emit_array(o, "int", "mk_kind", R, nr, [&](int r) { return std::to_string(m.rx[r].kind); });
+  emit_array(o, "double", "mk_lnA", R, nr, [&](int r) { return num(m.rx[r].lnA); });
+  emit_array(o, "double", "mk_b", R, nr, [&](int r) { return num(m.rx[r].b); });
+  emit_array(o, "double", "mk_th", R, nr, [&](int r) { return num(m.rx[r].theta); });
+  emit_array(o, "int", "mk_nre", R, nr, [&](int r) { return std::to_string(m.rx[r].nre); });
+  emit_array(o, "int", "mk_npr", R, nr, [&](int r) { return std::to_string(m.rx[r].npr); });
+  auto side_table = [&](const char* name, int ReactionData::*cnt, int (ReactionData::*arr)[kMaxSide]) {
+    o << "__device__ const int " << name << RP << " = {";
+    for (int r = 0; r < nr; ++r) {
+      o << (r ? "," : "") << "{";
+      for (int i = 0; i < kMaxSide; ++i) o << (i ? "," : "") << (i < m.rx[r].*cnt ? (m.rx[r].*arr)[i] : 0);
+      o << "}";
+    }
+    o << "};\n";
+  };
+  side_table("mk_rsp", &ReactionData::nre, &ReactionData::rsp);
+  side_table("mk_rnu", &ReactionData::nre, &ReactionData::rnu);
+  side_table("mk_psp", &ReactionData::npr, &ReactionData::psp);
+  side_table("mk_pnu", &ReactionData::npr, &ReactionData::pnu);
+  emit_array(o, "int", "mk_dnu", R, nr, [&](int r) {
+    int d = 0;
+    for (int i = 0; i < m.rx[r].npr; ++i) d += m.rx[r].pnu[i];
+    for (int i = 0; i < m.rx[r].nre; ++i) d -= m.rx[r].rnu[i];
+    return std::to_string(d);
+  });
+  std::vector<int> off(nr + 1, 0), esp;
+  std::vector<double> eval;
+  for (int r = 0; r < nr; ++r) {
+    off[r] = (int)esp.size();
+    if (m.rx[r].kind != 0)
+      for (auto& e : m.rx[r].eff)
+        if (e.second != 1.0) { esp.push_back(e.first); eval.push_back(e.second - 1.0); }
+  }
+  off[nr] = (int)esp.size();
+  const int ne = std::max<int>(1, (int)esp.size());
+  emit_array(o, "int", "mk_effoff", "[" + std::to_string(nr + 1) + "]", nr + 1, [&](int i) { return std::to_string(off[i]); });
+  emit_array(o, "int", "mk_effsp", "[" + std::to_string(ne) + "]", ne,
+             [&](int i) { return std::to_string(i < (int)esp.size() ? esp[i] : 0); });
+  emit_array(o, "double", "mk_effval", "[" + std::to_string(ne) + "]", ne,
+             [&](int i) { return num(i < (int)eval.size() ? eval[i] : 0.0); });
+  emit_array(o, "double", "mk_lnA0", R, nr, [&](int r) { return num(m.rx[r].lnA0); });
+  emit_array(o, "double", "mk_b0", R, nr, [&](int r) { return num(m.rx[r].b0); });
+  emit_array(o, "double", "mk_th0", R, nr, [&](int r) { return num(m.rx[r].theta0); });
+  o << "__device__ const double mk_troe[" << nr << "][4] = {";
+  for (int r = 0; r < nr; ++r) {
+    const double* t = m.rx[r].troe;
+    const bool tr = m.rx[r].kind == 3;
+    o << (r ? "," : "") << "{" << num(tr ? t[0] : 0.0) << "," << num(tr ? 1.0 / t[1] : 0.0) << ","
+      << num(tr ? 1.0 / t[2] : 0.0) << "," << num(tr ? t[3] : 0.0) << "}";
+  }
+  o << "};\n";
+  o << kDeviceSource;
+  o << "\nextern \"C\" __device__ const int chem_slots = SLOTS;\n";
+  return o.str();
+}
+
+// ------------------------------------------------------------------------------ NVRTC + cache
+
+uint64_t fnv1a(const std::string& s, uint64_t h = 1469598103934665603ULL) {
+  for (unsigned char c : s) { h ^= c; h *= 1099511628211ULL; }
+  return h;
+}
+
+const std::vector<std::string> kNvrtcOptions = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo",
+                                                "--ptxas-options=-v", "-DNDEBUG"};
+
+int nvrtc_compile(const std::string& src, const std::string& name, std::string* cubin, std::string* log) {
+  nvrtcProgram prog;
+  nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), name.c_str(), 0, nullptr, nullptr);
+  if (r != NVRTC_SUCCESS) return fail(CHEM_ENVRTC, "nvrtcCreateProgram: %s", nvrtcGetErrorString(r));
+  std::vector<const char*> opts;
+  for (auto& s : kNvrtcOptions) opts.push_back(s.c_str());
+  r = nvrtcCompileProgram(prog, (int)opts.size(), opts.data());
+  size_t logsz = 0;
+  nvrtcGetProgramLogSize(prog, &logsz);
+  std::string lg(logsz, '\0');
+  if (logsz) nvrtcGetProgramLog(prog, &lg[0]);
+  if (log) *log = lg;
+  if (r != NVRTC_SUCCESS) {
+    nvrtcDestroyProgram(&prog);
+    return fail(CHEM_ENVRTC, "NVRTC compile of %s failed: %s\n%s", name.c_str(), nvrtcGetErrorString(r),
+                lg.substr(0, 1500).c_str());
+  }
+  size_t n = 0;
+  nvrtcGetCUBINSize(prog, &n);
+  cubin->resize(n);
+  nvrtcGetCUBIN(prog, &(*cubin)[0]);
+  nvrtcDestroyProgram(&prog);
+  return 0;
+}
+
+// cubin for (mechanism, team, block): from cache_dir if present, else compiled (and stored)
+int build_cubin(const MechData& m, int team, int tpb, const char* cache_dir, bool verbose, std::string* cubin,
+                std::string* log) {
+  const std::string src = emit_mechanism(m, team, tpb);
+  int major = 0, minor = 0;
+  nvrtcVersion(&major, &minor);
+  std::string key = src;
+  for (auto& s : kNvrtcOptions) key += "|" + s;
+  key += "|nvrtc" + std::to_string(major) + "." + std::to_string(minor);
+  char hex[32];
+  snprintf(hex, sizeof(hex), "%016llx", (unsigned long long)fnv1a(key));
+  std::string path;
+  if (cache_dir && *cache_dir) {
+    path = std::string(cache_dir) + "/" + m.name + "_t" + std::to_string(team) + "_b" + std::to_string(tpb) + "_" +
+           hex + ".cubin";
+    std::ifstream in(path, std::ios::binary);
+    if (in) {
+      std::ostringstream ss;
+      ss << in.rdbuf();
+      *cubin = ss.str();
+      if (!cubin->empty()) return 0;
+    }
+  }
+  std::string lg;
+  int rc = nvrtc_compile(src, m.name + ".cu", cubin, &lg);
+  if (log) *log = lg;
+  if (verbose && !lg.empty()) fprintf(stderr, "[chem] %s team=%d block=%d\n%s\n", m.name.c_str(), team, tpb, lg.c_str());
+  if (rc) return rc;
+  if (!path.empty()) {
+    const std::string tmp = path + ".tmp" + std::to_string((long long)std::hash<std::string>{}(hex));
+    std::ofstream out(tmp, std::ios::binary);
+    out.write(cubin->data(), (std::streamsize)cubin->size());
+    out.close();
+    if (out) std::rename(tmp.c_str(), path.c_str());
+  }
+  return 0;
+}
+
+// ------------------------------------------------------------------------------ modules
+
+struct Module {
+  int team = 0, tpb = 0;
+  CUmodule mod = nullptr;
+  CUfunction f_source = nullptr, f_jac = nullptr, f_int = nullptr, f_pinit = nullptr, f_patt = nullptr,
+             f_pfin = nullptr;
+  int smem = 0;          // dynamic shared memory per block
+  int occ = 0;           // resident blocks per SM for f_int
+  int regs = 0;
+};
+
+}  // namespace
+
+struct chem_mech {
+  MechData data;
+  std::string cache_dir;
+  bool verbose = false;
+  CUcontext ctx = nullptr;
+  int n_sm = 0;
+  int default_team = 32, default_tpb = 64;
+  std::mutex mu;       // guards modules
+  std::mutex host_mu;  // guards the chem_integrate_host buffers
+  std::map<std::pair<int, int>, std::unique_ptr<Module>> modules;
+  // plain-mode host mirror of the activity counter and host-API buffers
+  unsigned int* pinned = nullptr;
+  CUdeviceptr host_api_buf = 0;
+  size_t host_api_bytes = 0;
+};
+
+namespace {
+
+int slots_for(int ns) { return ns * ns + 22 * ns + 16; }
+
+void default_config(int ns, int* team, int* tpb) {
+  if (ns <= 24) { *team = 32; *tpb = 128; }
+  else if (ns <= 64) { *team = 32; *tpb = 64; }
+  else { *team = 256; *tpb = 256; }
+}
+
+int check_config(int team, int tpb) {
+  if (team == 1 && (tpb == 32 || tpb == 64 || tpb == 128)) return 0;
+  if (team == 32 && tpb % 32 == 0 && tpb >= 32 && tpb <= 256) return 0;
+  if ((team == 64 || team == 128 || team == 256) && tpb == team) return 0;
+  return fail(CHEM_EARG, "unsupported kernel config team=%d block=%d", team, tpb);
+}
+
+int smem_bytes(int ns, int team, int tpb) {
+  const int teams = team == 1 ? tpb : (team == 32 ? tpb / 32 : 1);
+  return slots_for(ns) * 8 * teams;
+}
+
+int get_module(chem_mech* m, int team, int tpb, Module** out) {
+  std::lock_guard<std::mutex> lk(m->mu);
+  auto key = std::make_pair(team, tpb);
+  auto it = m->modules.find(key);
+  if (it != m->modules.end()) { *out = it->second.get(); return 0; }
+  if (int rc = check_config(team, tpb)) return rc;
+  const int ns = (int)m->data.sp.size();
+  const int smem = smem_bytes(ns, team, tpb);
+  int max_optin = 0;
+  CUdevice dev;
+  CU_TRY(drv::cuCtxGetDevice(&dev));
+  CU_TRY(drv::cuDeviceGetAttribute(&max_optin, CU_DEVICE_ATTRIBUTE_MAX_SHARED_MEMORY_PER_BLOCK_OPTIN, dev));
+  if (smem > max_optin)
+    return fail(CHEM_EARG, "config team=%d block=%d needs %d B shared memory (max %d)", team, tpb, smem, max_optin);
+  std::string cubin, log;
+  if (int rc = build_cubin(m->data, team, tpb, m->cache_dir.c_str(), m->verbose, &cubin, &log)) return rc;
+  auto mod = std::make_unique<Module>();
+  mod->team = team;
+  mod->tpb = tpb;
+  mod->smem = smem;
+  CU_TRY(drv::cuModuleLoadData(&mod->mod, cubin.data()));
+  CU_TRY(drv::cuModuleGetFunction(&mod->f_source, mod->mod, "chem_eval_source_k"));
+  CU_TRY(drv::cuModuleGetFunction(&mod->f_jac, mod->mod, "chem_eval_jacobian_k"));
+  CU_TRY(drv::cuModuleGetFunction(&mod->f_int, mod->mod, "chem_integrate_k"));
+  CU_TRY(drv::cuModuleGetFunction(&mod->f_pinit, mod->mod, "chem_plain_init_k"));
+  CU_TRY(drv::cuModuleGetFunction(&mod->f_patt, mod->mod, "chem_plain_attempt_k"));
+  CU_TRY(drv::cuModuleGetFunction(&mod->f_pfin, mod->mod, "chem_plain_finish_k"));
+  CUdeviceptr slots_ptr;
+  size_t slots_sz;
+  CU_TRY(drv::cuModuleGetGlobal(&slots_ptr, &slots_sz, mod->mod, "chem_slots"));
+  int dev_slots = 0;
+  CU_TRY(drv::cuMemcpyDtoH(&dev_slots, slots_ptr, sizeof(int)));
+  if (dev_slots != slots_for(ns)) return fail(CHEM_ECUDA, "shared-memory layout mismatch (%d vs %d)", dev_slots, slots_for(ns));
+  for (CUfunction f : {mod->f_source, mod->f_jac, mod->f_int, mod->f_pinit, mod->f_patt})
+    CU_TRY(drv::cuFuncSetAttribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem));
+  CU_TRY(drv::cuOccupancyMaxActiveBlocksPerMultiprocessor(&mod->occ, mod->f_int, tpb, smem));
+  CU_TRY(drv::cuFuncGetAttribute(&mod->regs, CU_FUNC_ATTRIBUTE_NUM_REGS, mod->f_int));
+  if (mod->occ < 1) return fail(CHEM_ECUDA, "config team=%d block=%d cannot be resident", team, tpb);
+  *out = mod.get();
+  m->modules[key] = std::move(mod);
+  return 0;
+}
+
+int resolve(chem_mech* m, const chem_int_opts* o, Module** mod) {
+  int team = m->default_team, tpb = m->default_tpb;
+  if (o && o->team > 0) {
+    team = o->team;
+    tpb = o->block > 0 ? o->block : (team == 1 ? 64 : (team == 32 ? 64 : team));
+  }
+  return get_module(m, team, tpb, mod);
+}
+
+int make_current(chem_mech* m) {
+  CU_TRY(drv::cuCtxSetCurrent(m->ctx));
+  return 0;
+}
+
+int teams_per_block(const Module* mod) { return mod->team == 1 ? mod->tpb : (mod->team == 32 ? mod->tpb / 32 : 1); }
+
+unsigned grid_for(const chem_mech* m, const Module* mod, int64_t n_cells) {
+  const int64_t tpb = teams_per_block(mod);
+  const int64_t need = (n_cells + tpb - 1) / tpb;
+  const int64_t cap = (int64_t)m->n_sm * mod->occ;
+  return (unsigned)std::max<int64_t>(1, std::min(need, cap));
+}
+
+int launch(CUfunction f, unsigned grid, const Module* mod, void* stream, void** args) {
+  CU_TRY(drv::cuLaunchKernel(f, grid, 1, 1, mod->tpb, 1, 1, mod->smem, (CUstream)stream, args, nullptr));
+  return 0;
+}
+
+int check_cells(int64_t n, int64_t ld) {
+  if (n < 0) return fail(CHEM_EARG, "n_cells < 0");
+  if (ld < n) return fail(CHEM_EARG, "ld (%lld) < n_cells (%lld)", (long long)ld, (long long)n);
+  return 0;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct PlainLayout {
+  size_t y, t, h, flags, att, st, cnt, total;
+};
+
+PlainLayout plain_layout(int ns, int64_t n, int max_steps) {
+  PlainLayout L;
+  size_t o = 0;
+  L.y = o; o = align256(o + sizeof(double) * ns * n);
+  L.t = o; o = align256(o + sizeof(double) * n);
+  L.h = o; o = align256(o + sizeof(double) * n);
+  L.flags = o; o = align256(o + sizeof(int) * n);
+  L.att = o; o = align256(o + sizeof(int) * n);
+  L.st = o; o = align256(o + sizeof(int) * n);
+  L.cnt = o; o = align256(o + sizeof(unsigned) * ((size_t)max_steps + 2));
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+// ================================================================================ C ABI
+
+extern "C" {
+
+const char* chem_last_error(void) { return g_last_error.c_str(); }
+
+int chem_mech_compile_only(const char* spec_path, const chem_build_opts* opts, char* log, size_t log_cap) {
+  if (!spec_path) return fail(CHEM_EARG, "spec_path is NULL");
+  MechData d;
+  if (int rc = read_spec(spec_path, &d)) return rc;
+  int team, tpb;
+  default_config((int)d.sp.size(), &team, &tpb);
+  if (opts && opts->team > 0) { team = opts->team; tpb = opts->block > 0 ? opts->block : tpb; }
+  if (int rc = check_config(team, tpb)) return rc;
+  std::string cubin, lg;
+  int rc = build_cubin(d, team, tpb, opts ? opts->cache_dir : nullptr, opts && opts->verbose, &cubin, &lg);
+  if (log && log_cap) {
+    const size_t n = std::min(lg.size(), log_cap - 1);
+    memcpy(log, lg.data(), n);
+    log[n] = '\0';
+  }
+  return rc;
+}
+
+int chem_mech_load(const char* spec_path, const chem_build_opts* opts, chem_mech_t* out) {
+  if (!spec_path || !out) return fail(CHEM_EARG, "NULL argument");
+  *out = nullptr;
+  auto m = std::make_unique<chem_mech>();
+  if (int rc = read_spec(spec_path, &m->data)) return rc;
+  if (opts && opts->cache_dir) m->cache_dir = opts->cache_dir;
+  m->verbose = opts && opts->verbose;
+  if (!drv::load()) return fail(CHEM_ECUDA, "%s", drv::load_error.c_str());
+  CU_TRY(drv::cuInit(0));
+  CUcontext ctx = nullptr;
+  CU_TRY(drv::cuCtxGetCurrent(&ctx));
+  if (!ctx) {
+    CUdevice dev;
+    CU_TRY(drv::cuDeviceGet(&dev, 0));
+    CU_TRY(drv::cuDevicePrimaryCtxRetain(&ctx, dev));
+    CU_TRY(drv::cuCtxSetCurrent(ctx));
+  }
+  m->ctx = ctx;
+  CUdevice dev;
+  CU_TRY(drv::cuCtxGetDevice(&dev));
+  CU_TRY(drv::cuDeviceGetAttribute(&m->n_sm, CU_DEVICE_ATTRIBUTE_MULTIPROCESSOR_COUNT, dev));
+  default_config((int)m->data.sp.size(), &m->default_team, &m->default_tpb);
+  if (opts && opts->team > 0) {
+    m->default_team = opts->team;
+    m->default_tpb = opts->block > 0 ? opts->block : m->default_tpb;
+  }
+  Module* mod;
+  if (int rc = get_module(m.get(), m->default_team, m->default_tpb, &mod)) return rc;
+  CU_TRY(drv::cuMemHostAlloc((void**)&m->pinned, 64 * sizeof(unsigned), 0));
+  *out = m.release();
+  return 0;
+}
+
+int chem_mech_free(chem_mech_t m) {
+  if (!m) return 0;
+  drv::cuCtxSetCurrent(m->ctx);
+  for (auto& kv : m->modules) drv::cuModuleUnload(kv.second->mod);
+  if (m->pinned) drv::cuMemFreeHost(m->pinned);
+  if (m->host_api_buf) drv::cuMemFree(m->host_api_buf);
+  delete m;
+  return 0;
+}
+
+int chem_mech_info(chem_mech_t m, int32_t* ns, int32_t* nr, int32_t* ne) {
+  if (!m) return fail(CHEM_EARG, "NULL mechanism");
+  if (ns) *ns = (int32_t)m->data.sp.size();
+  if (nr) *nr = (int32_t)m->data.rx.size();
+  if (ne) *ne = m->data.n_elements;
+  return 0;
+}
+
+int chem_mech_lnA(chem_mech_t m, double* lnA) {
+  if (!m || !lnA) return fail(CHEM_EARG, "NULL argument");
+  for (size_t r = 0; r < m->data.rx.size(); ++r) lnA[r] = m->data.rx[r].lnA;
+  return 0;
+}
+
+static int eval_common(chem_mech_t m, bool jac, int64_t n_cells, const double* T, const double* P,
+                       const double* n, double* out, int64_t ld, const double* lnA, void* stream) {
+  if (!m) return fail(CHEM_EARG, "NULL mechanism");
+  if (int rc = check_cells(n_cells, ld)) return rc;
+  if (n_cells == 0) return 0;
+  if (!T || !P || !n || !out) return fail(CHEM_EARG, "NULL array");
+  if (int rc = make_current(m)) return rc;
+  Module* mod;
+  if (int rc = resolve(m, nullptr, &mod)) return rc;
+  long long nc = n_cells, l = ld;
+  void* args[] = {&nc, (void*)&T, (void*)&P, (void*)&n, &out, &l, (void*)&lnA};
+  return launch(jac ? mod->f_jac : mod->f_source, grid_for(m, mod, n_cells), mod, stream, args);
+}
+
+int chem_eval_source(chem_mech_t m, int64_t n_cells, const double* T, const double* P, const double* n, double* f,
+                     int64_t ld, const double* lnA, void* stream) {
+  return eval_common(m, false, n_cells, T, P, n, f, ld, lnA, stream);
+}
+
+int chem_eval_jacobian(chem_mech_t m, int64_t n_cells, const double* T, const double* P, const double* n, double* J,
+                       int64_t ld, const double* lnA, void* stream) {
+  return eval_common(m, true, n_cells, T, P, n, J, ld, lnA, stream);
+}
+
+size_t chem_integrate_workspace(chem_mech_t m, int64_t n_cells, const chem_int_opts* o) {
+  if (!m || n_cells < 0) return 0;
+  const int mode = o ? o->mode : CHEM_MODE_PERSISTENT;
+  if (mode == CHEM_MODE_PLAIN) {
+    const int max_steps = (o && o->max_steps > 0) ? o->max_steps : 100000;
+    return plain_layout((int)m->data.sp.size(), n_cells, max_steps).total;
+  }
+  return 256;
+}
+
+int chem_kernel_config(chem_mech_t m, const chem_int_opts* o, int32_t* team, int32_t* block, int32_t* smem,
+                       int32_t* regs) {
+  if (!m) return fail(CHEM_EARG, "NULL mechanism");
+  if (int rc = make_current(m)) return rc;
+  Module* mod;
+  if (int rc = resolve(m, o, &mod)) return rc;
+  if (team) *team = mod->team;
+  if (block) *block = mod->tpb;
+  if (smem) *smem = mod->smem;
+  if (regs) *regs = mod->regs;
+  return 0;
+}
+
+int chem_integrate(chem_mech_t m, int64_t n_cells, double* T, const double* P, double* Y, int64_t ld, double dt,
+                   double rtol, double atol, double* h, int32_t* status, const chem_int_opts* o, void* ws,
+                   size_t ws_bytes, void* stream) {
+  if (!m) return fail(CHEM_EARG, "NULL mechanism");
+  if (int rc = check_cells(n_cells, ld)) return rc;
+  if (!(dt > 0) || !(rtol > 0) || !(atol > 0) || !std::isfinite(dt))
+    return fail(CHEM_EARG, "dt, rtol and atol must be positive and finite");
+  if (n_cells == 0) return 0;
+  if (!T || !P || !Y) return fail(CHEM_EARG, "NULL array");
+  const int mode = o ? o->mode : CHEM_MODE_PERSISTENT;
+  int max_steps = (o && o->max_steps > 0) ? o->max_steps : 100000;
+  double h_min = (o && o->h_min > 0) ? o->h_min : 1e-20;
+  double T_min = o ? o->T_min : 0.0;
+  const double* lnA = o ? o->lnA : nullptr;
+  int* att = o ? o->attempts : nullptr;
+  const size_t need = chem_integrate_workspace(m, n_cells, o);
+  if (!ws || ws_bytes < need) return fail(CHEM_EWS, "workspace of %zu bytes needed, %zu given", need, ws_bytes);
+  if (((uintptr_t)ws) & 255) return fail(CHEM_EARG, "workspace must be 256-byte aligned");
+  if (int rc = make_current(m)) return rc;
+  Module* mod;
+  if (int rc = resolve(m, o, &mod)) return rc;
+  long long nc = n_cells, l = ld;
+  CUstream s = (CUstream)stream;
+  if (mode == CHEM_MODE_PERSISTENT) {
+    CUdeviceptr q = (CUdeviceptr)ws;
+    CU_TRY(drv::cuMemsetD32Async(q, 0, 2, s));
+    void* args[] = {&nc, &T, (void*)&P, &Y, &l, &dt, &rtol, &atol, &h, &status, &att, (void*)&lnA,
+                    &max_steps, &h_min, &T_min, &q};
+    return launch(mod->f_int, grid_for(m, mod, n_cells), mod, stream, args);
+  }
+  if (mode != CHEM_MODE_PLAIN) return fail(CHEM_EARG, "unknown mode %d", mode);
+  // plain driver: init, then one launch per attempt until no cell is active
+  const int ns = (int)m->data.sp.size();
+  PlainLayout L = plain_layout(ns, n_cells, max_steps);
+  char* base = (char*)ws;
+  double* wy = (double*)(base + L.y);
+  double* wt = (double*)(base + L.t);
+  double* wh = (double*)(base + L.h);
+  int* wfl = (int*)(base + L.flags);
+  int* wat = (int*)(base + L.att);
+  int* wst = (int*)(base + L.st);
+  unsigned* cnt = (unsigned*)(base + L.cnt);
+  CU_TRY(drv::cuMemsetD32Async((CUdeviceptr)cnt, 0, (size_t)max_steps + 2, s));
+  const unsigned grid = grid_for(m, mod, n_cells);
+  {
+    void* args[] = {&nc, &T, &Y, &l, &dt, (void*)&h, &T_min, &wy, &wt, &wh, &wfl, &wat, &wst};
+    if (int rc = launch(mod->f_pinit, grid, mod, stream, args)) return rc;
+  }
+  {
+    void* args[] = {&nc, &status, &att, &wst, &wfl};
+    CU_TRY(drv::cuLaunchKernel(mod->f_pfin, (unsigned)((n_cells + 255) / 256), 1, 1, 256, 1, 1, 0, s, args, nullptr));
+  }
+  // the attempt counter of every active cell grows by one per launch, so max_steps + 1
+  // launches retire every cell; the host checks the activity counter every few launches
+  const int poll = 4;
+  for (int it = 0; it <= max_steps; ++it) {
+    unsigned* c = cnt + it;
+    void* args[] = {&nc, &T, (void*)&P, &Y, &l, &dt, &rtol, &atol, &h, &status, &att, (void*)&lnA,
+                    &max_steps, &h_min, &wy, &wt, &wh, &wfl, &wat, &wst, &c};
+    if (int rc = launch(mod->f_patt, grid, mod, stream, args)) return rc;
+    if (it % poll == poll - 1 || it == max_steps) {
+      CU_TRY(drv::cuMemcpyDtoHAsync(m->pinned, (CUdeviceptr)c, sizeof(unsigned), s));
+      CU_TRY(drv::cuStreamSynchronize(s));
+      if (m->pinned[0] == 0) break;
+    }
+  }
+  return 0;
+}
+
+int chem_integrate_host(chem_mech_t m, int64_t n_cells, double* T, const double* P, double* Y, double dt, double rtol,
+                        double atol, double* h, int32_t* status, const chem_int_opts* o, void* stream) {
+  if (!m) return fail(CHEM_EARG, "NULL mechanism");
+  if (n_cells <= 0) return n_cells == 0 ? 0 : fail(CHEM_EARG, "n_cells < 0");
+  if (!T || !P || !Y) return fail(CHEM_EARG, "NULL array");
+  if (int rc = make_current(m)) return rc;
+  const int ns = (int)m->data.sp.size();
+  chem_int_opts oo = o ? *o : chem_int_opts{};
+  oo.mode = CHEM_MODE_PERSISTENT;
+  oo.attempts = nullptr;
+  const size_t n = (size_t)n_cells;
+  const size_t offT = 0, offP = align256(offT + 8 * n), offY = align256(offP + 8 * n),
+               offH = align256(offY + 8 * n * ns), offS = align256(offH + 8 * n), offW = align256(offS + 4 * n);
+  const size_t total = offW + 256;
+  std::lock_guard<std::mutex> lk(m->host_mu);
+  if (m->host_api_bytes < total) {
+    if (m->host_api_buf) CU_TRY(drv::cuMemFree(m->host_api_buf));
+    m->host_api_buf = 0;
+    m->host_api_bytes = 0;
+    CU_TRY(drv::cuMemAlloc(&m->host_api_buf, total));
+    m->host_api_bytes = total;
+  }
+  CUstream s = (CUstream)stream;
+  const CUdeviceptr b = m->host_api_buf;
+  CU_TRY(drv::cuMemcpyHtoDAsync(b + offT, T, 8 * n, s));
+  CU_TRY(drv::cuMemcpyHtoDAsync(b + offP, P, 8 * n, s));
+  CU_TRY(drv::cuMemcpyHtoDAsync(b + offY, Y, 8 * n * ns, s));
+  if (h) CU_TRY(drv::cuMemcpyHtoDAsync(b + offH, h, 8 * n, s));
+  int rc = chem_integrate(m, n_cells, (double*)(b + offT), (const double*)(b + offP), (double*)(b + offY), n_cells,
+                          dt, rtol, atol, h ? (double*)(b + offH) : nullptr, status ? (int32_t*)(b + offS) : nullptr,
+                          &oo, (void*)(b + offW), 256, stream);
+  if (rc) return rc;
+  CU_TRY(drv::cuMemcpyDtoHAsync(T, b + offT, 8 * n, s));
+  CU_TRY(drv::cuMemcpyDtoHAsync(Y, b + offY, 8 * n * ns, s));
+  if (h) CU_TRY(drv::cuMemcpyDtoHAsync(h, b + offH, 8 * n, s));
+  if (status) CU_TRY(drv::cuMemcpyDtoHAsync(status, b + offS, 4 * n, s));
+  CU_TRY(drv::cuStreamSynchronize(s));
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,955 @@
+// Device code of the batched ROS4 chemistry integrator (FP64, sm_103a).
+//
+// Compiled at run time by NVRTC, once per mechanism and launch configuration, after a
+// generated header (chem_host.cpp, emit_mechanism) that defines:
+//   NS, NR            species and reactions; the state length is NS ([T, n_1..n_{NS-1}])
+//   TEAM, TPB         lanes per cell (1, 32 or TPB) and threads per block
+//   MAXP              largest number of distinct species on one side of a reaction
+//   tables mk_*       NASA-7 coefficients pre-divided for cp, h and s; Arrhenius data; species
+//                     lists; efficiencies; falloff data (see emit_mechanism)
+//
+// What the kernels compute (Curtis, Niemeyer & Sung):
+//   * f(y), Sec. 2.1 Eq. (e:dphidt): concentrations from the unit-mass closure of Eq. (e:n_nsp);
+//     NASA-7 thermo; Arrhenius / third-body / Lindemann / Troe forward rates; reverse rates from
+//     the equilibrium constant; net production rates; dT/dt from the constant-pressure energy
+//     balance;
+//   * the analytical Jacobian J = df/dy, Eq. (e:jac), in closed form: the reaction part
+//     d(omega)/dC (sparse scatter plus the dense third-body efficiency part), then the chain
+//     rule to the [T, n] state (the bath-gas column, the volume terms and the temperature row);
+//   * the transformed ROS4 step of Sec. 2.3 with partial-pivoting LU of (I/(gamma h) - J), four
+//     stage solves (three f evaluations: the Hairer-Wanner set repeats stage 3's argument for
+//     stage 4), the embedded error estimate and the step-size controller;
+//   * batching (Sec. 2.4.1): a persistent kernel whose teams pull cells from a device work
+//     queue, and a plain form that runs one step attempt per launch.
+//
+// Work decomposition.  A "team" of TEAM threads owns one cell at a time; all of the cell's
+// working set (the N x N matrix, stage vectors, thermo and rate scratch) sits in shared memory.
+// TEAM == 1: one thread per cell, arrays interleaved across the block's threads (stride TPB)
+// so that lane-consecutive accesses hit consecutive banks.  TEAM == 32: a warp per cell,
+// contiguous arrays.  TEAM == TPB (64..256): a block per cell.  Reaction loops give each lane a
+// subset of reactions and scatter into the shared Jacobian with shared-memory atomics (TEAM>1).
+// Every device loop is bounded; there is no grid-wide wait.
+
+#define ELEM 0
+#define THIRD 1
+#define LIND 2
+#define TROE 3
+
+#define R_U 8314.462618
+#define P_ATM 101325.0
+#define LN10 2.302585092994046
+
+#define ST_OK 0
+#define ST_MAX_STEPS 1
+#define ST_H_UNDERFLOW 2
+#define ST_NONFINITE 3
+#define ST_SKIPPED 4
+
+#define NEQ NS
+#define BATH (NS - 1)
+
+#if TEAM == 1
+#define SS TPB
+#define NTEAM TPB
+#elif TEAM == 32
+#define SS 1
+#define NTEAM (TPB / 32)
+#else
+#define SS 1
+#define NTEAM 1
+#endif
+
+// per-cell shared-memory slots (units of SS doubles)
+#define OFF_A 0
+#define OFF_Y (OFF_A + NEQ * NEQ)
+#define OFF_YT (OFF_Y + NEQ)
+#define OFF_F (OFF_YT + NEQ)
+#define OFF_U (OFF_F + NEQ)
+#define OFF_INVD (OFF_U + 4 * NEQ)
+#define OFF_TMP (OFF_INVD + NEQ)
+#define OFF_C (OFF_TMP + NEQ)
+#define OFF_CP (OFF_C + NS)
+#define OFF_HRT (OFF_CP + NS)
+#define OFF_EX (OFF_HRT + NS)
+#define OFF_IEX (OFF_EX + NS)
+#define OFF_DCP (OFF_IEX + NS)
+#define OFF_OM (OFF_DCP + NS)
+#define OFF_DOMT (OFF_OM + NS)
+#define OFF_BK (OFF_DOMT + NS)
+#define OFF_AL (OFF_BK + NS)
+#define OFF_BE (OFF_AL + NS)
+#define OFF_JT (OFF_BE + NS)
+#define OFF_PIV (OFF_JT + NS)
+#define OFF_RED (OFF_PIV + NEQ)
+#define SLOTS (OFF_RED + 16)
+
+// ------------------------------------------------------------------------------ team plumbing
+
+__device__ __forceinline__ void tsync() {
+#if TEAM == 32
+  __syncwarp();
+#elif TEAM > 32
+  __syncthreads();
+#endif
+}
+
+struct Team {
+  double* base;  // element i of array at slot offset o: base[(o + i) * SS]
+  int tl;        // lane within the team
+  __device__ __forceinline__ double& at(int o, int i) const { return base[(o + i) * SS]; }
+  __device__ __forceinline__ double& A(int i, int j) const { return base[(OFF_A + i * NEQ + j) * SS]; }
+  __device__ __forceinline__ int& piv(int i) const { return *reinterpret_cast<int*>(&base[(OFF_PIV + i) * SS]); }
+};
+
+// sum over the team; every lane gets the same bits (butterfly with commutative adds)
+__device__ __forceinline__ double team_sum(const Team& tm, double v) {
+#if TEAM == 1
+  return v;
+#else
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+#if TEAM > 32
+  double* red = &tm.base[OFF_RED];
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = 0.0;
+  for (int w = 0; w < TEAM / 32; ++w) v += red[w];
+  __syncthreads();
+#endif
+  return v;
+#endif
+}
+
+// any-lane flag over the team
+__device__ __forceinline__ bool team_any(const Team& tm, bool f) {
+#if TEAM == 1
+  return f;
+#elif TEAM == 32
+  return __any_sync(0xffffffffu, f);
+#else
+  return __syncthreads_or(f) != 0;
+#endif
+}
+
+template <class T>
+__device__ __forceinline__ void scatter_add(double* p, double v) {
+#if TEAM == 1
+  *p += v;
+#else
+  atomicAdd(p, v);
+#endif
+}
+
+// |x| as an order-preserving integer (integer pipe instead of the FP64 pipe)
+__device__ __forceinline__ long long abs_key(double x) {
+  return __double_as_longlong(x) & 0x7fffffffffffffffLL;
+}
+
+// ------------------------------------------------------------------------------ thermo + C
+
+// Concentrations, thermo per species and mixture sums for state y (slot OFF_Y or OFF_YT).
+// Returns V; writes C, cp, h/RT, exp(s/R - h/RT), its inverse and (WJ) dcp/dT.
+struct CellScalars {
+  double T, invT, lnT, V, cpm, dcpm;  // cpm = sum n_k cp_k / R, dcpm = sum n_k dcp_k/dT / R
+};
+
+template <bool WJ>
+__device__ __forceinline__ void thermo_conc(const Team& tm, int oy, double P, CellScalars& cs) {
+  const double T = tm.at(oy, 0);
+  const double invT = 1.0 / T;
+  const double lnT = log(T);
+  // mass closure: n_bath = (1 - sum_k W_k n_k) / W_bath; n_tot = sum of all moles
+  double wsum = 0.0, nsum = 0.0;
+  for (int k = tm.tl; k < NS - 1; k += TEAM) {
+    const double n = tm.at(oy, 1 + k);
+    wsum += mk_W[k] * n;
+    nsum += n;
+  }
+  wsum = team_sum(tm, wsum);
+  nsum = team_sum(tm, nsum);
+  const double nb = (1.0 - wsum) * mk_invW[BATH];
+  const double ntot = nsum + nb;
+  const double V = ntot * R_U * T / P;
+  const double invV = 1.0 / V;
+  double cpm = 0.0, dcpm = 0.0;
+  for (int k = tm.tl; k < NS; k += TEAM) {
+    const double n = k < NS - 1 ? tm.at(oy, 1 + k) : nb;
+    tm.at(OFF_C, k) = n * invV;
+    const int r = T < mk_Tmid[k] ? 0 : 1;
+    const double* c = mk_cp[k][r];
+    const double* hh = mk_h[k][r];
+    const double* s = mk_s[k][r];
+    const double cp = c[0] + T * (c[1] + T * (c[2] + T * (c[3] + T * c[4])));
+    const double hRT = hh[0] + T * (hh[1] + T * (hh[2] + T * (hh[3] + T * hh[4]))) + hh[5] * invT;
+    const double sR = s[0] * lnT + s[6] + T * (s[1] + T * (s[2] + T * (s[3] + T * s[4])));
+    tm.at(OFF_CP, k) = cp;
+    tm.at(OFF_HRT, k) = hRT;
+    const double ex = exp(sR - hRT);
+    tm.at(OFF_EX, k) = ex;
+    tm.at(OFF_IEX, k) = 1.0 / ex;
+    cpm += n * cp;
+    if (WJ) {
+      const double* d = mk_dcp[k][r];
+      const double dcp = d[0] + T * (d[1] + T * (d[2] + T * d[3]));
+      tm.at(OFF_DCP, k) = dcp;
+      dcpm += n * dcp;
+    }
+  }
+  cs.T = T;
+  cs.invT = invT;
+  cs.lnT = lnT;
+  cs.V = V;
+  cs.cpm = team_sum(tm, cpm);
+  if (WJ) cs.dcpm = team_sum(tm, dcpm);
+  tsync();
+}
+
+// ------------------------------------------------------------------------------ reactions
+
+// species index -> row/column of the state matrix: species 0..NS-2 -> 1..NS-1, bath -> 0
+__device__ __forceinline__ int smap(int k) { return k == BATH ? 0 : k + 1; }
+
+// Net production rates omega (slot OFF_OM, zeroed by the caller) and, with WJ, the reaction
+// part of the Jacobian: A[smap(k)][smap(j)] += d omega_k / d C_j (without the default-
+// efficiency third-body part, which is collected per species in OFF_BK), d omega_k/dT at
+// constant C in OFF_DOMT.  The caller zeroes A, OFF_DOMT and OFF_BK.
+template <bool WJ>
+__device__ __forceinline__ void reaction_loop(const Team& tm, const CellScalars& cs, double P,
+                                              const double* __restrict__ lnA_ext) {
+  const double T = cs.T, invT = cs.invT, lnT = cs.lnT;
+  const double Ctot = P * invT / R_U;       // sum_k C_k = P / (R T)
+  const double rtp = R_U * T / P_ATM;       // (P_atm / R T)^-1
+  const double irtp = 1.0 / rtp;
+  for (int r = tm.tl; r < NR; r += TEAM) {
+    const int kind = mk_kind[r];
+    const double lA = lnA_ext ? lnA_ext[r] : mk_lnA[r];
+    const double kinf = exp(lA + mk_b[r] * lnT - mk_th[r] * invT);
+    double kf = kinf;
+    double dlkf_dT = 0.0, dlkf_dM = 0.0;
+    double M = 0.0;
+    if (WJ) dlkf_dT = (mk_b[r] + mk_th[r] * invT) * invT;
+    if (kind != ELEM) {
+      M = Ctot;
+      for (int e = mk_effoff[r]; e < mk_effoff[r + 1]; ++e) M += mk_effval[e] * tm.at(OFF_C, mk_effsp[e]);
+    }
+    if (kind >= LIND) {
+      const double k0 = exp(mk_lnA0[r] + mk_b0[r] * lnT - mk_th0[r] * invT);
+      double Pr = k0 * M / kinf;
+      bool floored = false;
+      if (Pr < 1e-300) { Pr = 1e-300; floored = true; }
+      double F = 1.0, dlF_dlPr = 0.0, dlF_dT = 0.0;
+      if (kind == TROE) {
+        const double a = mk_troe[r][0];
+        const double e3 = exp(-T * mk_troe[r][1]);
+        const double e1 = exp(-T * mk_troe[r][2]);
+        const double T2 = mk_troe[r][3];
+        const double e2 = T2 > 0.0 ? exp(-T2 * invT) : 0.0;
+        const double Fc = (1.0 - a) * e3 + a * e1 + e2;
+        const double lFc = log10(Fc);
+        const double c = -0.4 - 0.67 * lFc;
+        const double n = 0.75 - 1.27 * lFc;
+        const double x = log10(Pr) + c;
+        const double d = n - 0.14 * x;
+        const double id = 1.0 / d;
+        const double f1 = x * id;
+        const double den = 1.0 / (1.0 + f1 * f1);
+        const double lF = lFc * den;
+        F = exp(lF * LN10);
+        if (WJ) {
+          const double g2 = 2.0 * lFc * f1 * den * den;  // -d log10F / d f1
+          if (!floored) dlF_dlPr = -g2 * n * id * id;
+          const double dFc = -(1.0 - a) * mk_troe[r][1] * e3 - a * mk_troe[r][2] * e1 +
+                             (T2 > 0.0 ? T2 * invT * invT * e2 : 0.0);
+          const double df1_dlFc = (-0.67 * n + 1.27 * x) * id * id;
+          const double dlog10F_dlFc = den - g2 * df1_dlFc;
+          dlF_dT = dlog10F_dlFc * dFc / Fc;
+        }
+      }
+      kf = kinf * (Pr / (1.0 + Pr)) * F;
+      if (WJ) {
+        const double g = floored ? 0.0 : 1.0 / (1.0 + Pr) + dlF_dlPr;
+        const double dlk0 = (mk_b0[r] + mk_th0[r] * invT) * invT;
+        dlkf_dM = g / M;
+        dlkf_dT = dlkf_dT + g * (dlk0 - dlkf_dT) + dlF_dT;
+      }
+    }
+    // reverse constant: k_r = k_f / K_c with K_c = prod exp(s/R - h/RT)^nu (P_atm/RT)^dnu
+    double kr = kf;
+    double fwd = kf;
+    const int nre = mk_nre[r], npr = mk_npr[r];
+    for (int i = 0; i < nre; ++i) {
+      const int sp = mk_rsp[r][i];
+      const double c = tm.at(OFF_C, sp), ex = tm.at(OFF_EX, sp);
+      for (int v = 0; v < mk_rnu[r][i]; ++v) { fwd *= c; kr *= ex; }
+    }
+    double rev = 1.0;
+    for (int i = 0; i < npr; ++i) {
+      const int sp = mk_psp[r][i];
+      const double c = tm.at(OFF_C, sp), iex = tm.at(OFF_IEX, sp);
+      for (int v = 0; v < mk_pnu[r][i]; ++v) { rev *= c; kr *= iex; }
+    }
+    const int dnu = mk_dnu[r];
+    for (int v = 0; v < dnu; ++v) kr *= rtp;
+    for (int v = 0; v < -dnu; ++v) kr *= irtp;
+    rev *= kr;
+    const double m = kind == THIRD ? M : 1.0;
+    const double qnet = fwd - rev;
+    const double q = m * qnet;
+    for (int i = 0; i < nre; ++i) scatter_add<double>(&tm.at(OFF_OM, mk_rsp[r][i]), -mk_rnu[r][i] * q);
+    for (int i = 0; i < npr; ++i) scatter_add<double>(&tm.at(OFF_OM, mk_psp[r][i]), mk_pnu[r][i] * q);
+    if (WJ) {
+      // d ln Kc / dT = (sum nu'' h/RT - sum nu' h/RT - dnu) / T
+      double dlKc = -dnu;
+      for (int i = 0; i < npr; ++i) dlKc += mk_pnu[r][i] * tm.at(OFF_HRT, mk_psp[r][i]);
+      for (int i = 0; i < nre; ++i) dlKc -= mk_rnu[r][i] * tm.at(OFF_HRT, mk_rsp[r][i]);
+      dlKc *= invT;
+      const double dqdT = m * (fwd * dlkf_dT - rev * (dlkf_dT - dlKc));
+      // dq/d[M]: the [M] factor of THIRD reactions, the falloff blend of LIND/TROE
+      const double beta = kind == THIRD ? qnet : (kind == ELEM ? 0.0 : qnet * dlkf_dM);
+      // dq/dC_j of the mass-action products
+      double dq[2 * MAXP];
+      int dsp[2 * MAXP];
+      int nd = 0;
+      for (int i = 0; i < nre; ++i) {
+        const int nu = mk_rnu[r][i];
+        double p = m * kf * nu;
+        for (int i2 = 0; i2 < nre; ++i2) {
+          const double c = tm.at(OFF_C, mk_rsp[r][i2]);
+          const int e = i2 == i ? nu - 1 : mk_rnu[r][i2];
+          for (int v = 0; v < e; ++v) p *= c;
+        }
+        dq[nd] = p;
+        dsp[nd++] = mk_rsp[r][i];
+      }
+      for (int i = 0; i < npr; ++i) {
+        const int nu = mk_pnu[r][i];
+        double p = -m * kr * nu;
+        for (int i2 = 0; i2 < npr; ++i2) {
+          const double c = tm.at(OFF_C, mk_psp[r][i2]);
+          const int e = i2 == i ? nu - 1 : mk_pnu[r][i2];
+          for (int v = 0; v < e; ++v) p *= c;
+        }
+        dq[nd] = p;
+        dsp[nd++] = mk_psp[r][i];
+      }
+      for (int side = 0; side < 2; ++side) {
+        const int np = side == 0 ? nre : npr;
+        for (int i = 0; i < np; ++i) {
+          const int k = side == 0 ? mk_rsp[r][i] : mk_psp[r][i];
+          const double nuk = side == 0 ? -mk_rnu[r][i] : mk_pnu[r][i];
+          const int row = smap(k);
+          for (int d = 0; d < nd; ++d) scatter_add<double>(&tm.A(row, smap(dsp[d])), nuk * dq[d]);
+          scatter_add<double>(&tm.at(OFF_DOMT, k), nuk * dqdT);
+          if (kind != ELEM) {
+            scatter_add<double>(&tm.at(OFF_BK, k), nuk * beta);
+            for (int e = mk_effoff[r]; e < mk_effoff[r + 1]; ++e)
+              scatter_add<double>(&tm.A(row, smap(mk_effsp[e])), nuk * beta * mk_effval[e]);
+          }
+        }
+      }
+    }
+  }
+  tsync();
+}
+
+// f from omega: f[0] = dT/dt = -T sum_k (h_k/RT) V omega_k / sum_k n_k cp_k/R,
+// f[1+k] = V omega_k.  Returns dT/dt.
+__device__ __forceinline__ double source_from_omega(const Team& tm, const CellScalars& cs, int of) {
+  double hs = 0.0;
+  for (int k = tm.tl; k < NS; k += TEAM) {
+    const double om = tm.at(OFF_OM, k);
+    hs += tm.at(OFF_HRT, k) * om;
+    if (k < NS - 1) tm.at(of, 1 + k) = cs.V * om;
+  }
+  hs = team_sum(tm, hs);
+  const double fT = -cs.T * cs.V * hs / cs.cpm;
+  if (tm.tl == 0) tm.at(of, 0) = fT;
+  tsync();
+  return fT;
+}
+
+__device__ __forceinline__ void zero_rates(const Team& tm, bool with_j) {
+  for (int k = tm.tl; k < NS; k += TEAM) {
+    tm.at(OFF_OM, k) = 0.0;
+    if (with_j) { tm.at(OFF_DOMT, k) = 0.0; tm.at(OFF_BK, k) = 0.0; }
+  }
+  if (with_j)
+    for (int e = tm.tl; e < NEQ * NEQ; e += TEAM) tm.at(OFF_A, e) = 0.0;
+  tsync();
+}
+
+// f(y) into slot `of` for the state at slot `oy`.
+__device__ void eval_f(const Team& tm, int oy, int of, double P, const double* lnA_ext) {
+  CellScalars cs;
+  thermo_conc<false>(tm, oy, P, cs);
+  zero_rates(tm, false);
+  reaction_loop<false>(tm, cs, P, lnA_ext);
+  source_from_omega(tm, cs, of);
+}
+
+// f(y) into `of` and the state Jacobian into A: A = sgn * J + shift * I.
+// sgn = +1, shift = 0 gives J; sgn = -1, shift = 1/(gamma h) gives M = I/(gamma h) - J.
+__device__ void eval_f_jac(const Team& tm, int oy, int of, double P, const double* lnA_ext,
+                           double sgn, double shift) {
+  CellScalars cs;
+  thermo_conc<true>(tm, oy, P, cs);
+  zero_rates(tm, true);
+  reaction_loop<true>(tm, cs, P, lnA_ext);
+  const double fT = source_from_omega(tm, cs, of);
+  const double T = cs.T, V = cs.V, invT = cs.invT;
+  const double RTP = R_U * T / P;
+  const double Ctot = P * invT / R_U;
+  // per species row k (B_k = default-efficiency third-body part, added to every column):
+  //   D_k = omega_k - sum_m (d omega_k/dC_m) C_m,
+  //   d f_k/d n_j = d omega_k/dC_j - w_j d omega_k/dC_bath + (RT/P)(1 - w_j) D_k
+  //               = A_kj + P1_k - w_j P2_k with P1 = B_k + (RT/P) D_k, P2 = A_kb + B_k + (RT/P) D_k,
+  //   d f_k / dT = V (D_k / T + d omega_k/dT).
+  for (int k = tm.tl; k < NS; k += TEAM) {
+    const int row = smap(k);
+    double dot = 0.0;
+    for (int j = 0; j < NS; ++j) dot += tm.A(row, smap(j)) * tm.at(OFF_C, j);
+    const double Bk = tm.at(OFF_BK, k);
+    const double D = tm.at(OFF_OM, k) - dot - Bk * Ctot;
+    tm.at(OFF_AL, k) = tm.A(row, 0) + Bk + RTP * D;
+    tm.at(OFF_BE, k) = Bk + RTP * D;
+    tm.at(OFF_JT, k) = V * (D * invT + tm.at(OFF_DOMT, k));
+  }
+  tsync();
+  // species rows, w_j = W_j / W_bath
+#if TEAM == 1
+  for (int i = 1; i < NEQ; ++i) {
+    const int k = i - 1;
+    const double al = tm.at(OFF_AL, k), be = tm.at(OFF_BE, k);
+    for (int l = 1; l < NEQ; ++l) {
+      const double w = mk_wratio[l - 1];
+      const double J = tm.A(i, l) - w * al + be;
+      tm.A(i, l) = sgn * J + (i == l ? shift : 0.0);
+    }
+    tm.A(i, 0) = sgn * tm.at(OFF_JT, k);
+  }
+#else
+  for (int e = tm.tl; e < (NEQ - 1) * NEQ; e += TEAM) {
+    const int i = 1 + e / NEQ, l = e - (i - 1) * NEQ;
+    const int k = i - 1;
+    if (l == 0) {
+      tm.A(i, 0) = sgn * tm.at(OFF_JT, k);
+    } else {
+      const double w = mk_wratio[l - 1];
+      const double J = tm.A(i, l) - w * tm.at(OFF_AL, k) + tm.at(OFF_BE, k);
+      tm.A(i, l) = sgn * J + (i == l ? shift : 0.0);
+    }
+  }
+#endif
+  tsync();
+  // temperature row: f_T = -Q / cpm with Q = T sum_k (h_k/RT) f'_k over all species (f'_k =
+  // V omega_k, bath included); dQ/dn_j = T sum_k (h_k/RT) J_kj, dQ/dT = sum_k cp_k f'_k +
+  // T sum_k (h_k/RT) J_kT; d cpm/dn_j = cp_j - w_j cp_bath, d cpm/dT = sum_k n_k dcp_k/dT.
+  const double hb = tm.at(OFF_HRT, BATH), alb = tm.at(OFF_AL, BATH), beb = tm.at(OFF_BE, BATH);
+  const double icpm = 1.0 / cs.cpm;
+  for (int l = tm.tl; l < NEQ; l += TEAM) {
+    double s = 0.0;
+    for (int i = 1; i < NEQ; ++i) s += tm.at(OFF_HRT, i - 1) * tm.A(i, l);
+    if (l > 0) s -= tm.at(OFF_HRT, l - 1) * shift;  // remove the diagonal shift of M
+    s *= sgn;  // the rows above carry the sign
+    double val;
+    if (l == 0) {
+      s += hb * tm.at(OFF_JT, BATH);
+      double cpf = 0.0;
+      for (int k = 0; k < NS; ++k) cpf += tm.at(OFF_CP, k) * tm.at(OFF_OM, k);
+      const double dQdT = cpf * V + T * s;
+      val = -(dQdT + fT * cs.dcpm) * icpm;
+    } else {
+      const double w = mk_wratio[l - 1];
+      const double Jb = tm.A(0, l) - w * alb + beb;  // bath row, before it is overwritten
+      s += hb * Jb;
+      const double dcpm = tm.at(OFF_CP, l - 1) - w * tm.at(OFF_CP, BATH);
+      val = -(T * s + fT * dcpm) * icpm;
+    }
+    tm.A(0, l) = sgn * val + (l == 0 ? shift : 0.0);
+  }
+  tsync();
+}
+
+// ------------------------------------------------------------------------------ LU + solves
+
+// In-place LU with partial pivoting of A (N x N): largest |a| in the column, lowest row on
+// ties.  Pivots in OFF_PIV (row swapped with k at step k), 1/U_kk in OFF_INVD, and the
+// composed permutation in OFF_TMP (as ints in the PIV slots' neighbours is avoided: TMP holds
+// perm as doubles of exact small integers).
+__device__ void lu_factor(const Team& tm) {
+#if TEAM == 1
+  for (int k = 0; k < NEQ; ++k) {
+    int p = k;
+    long long best = abs_key(tm.A(k, k));
+    for (int i = k + 1; i < NEQ; ++i) {
+      const long long v = abs_key(tm.A(i, k));
+      if (v > best) { best = v; p = i; }
+    }
+    tm.piv(k) = p;
+    if (p != k)
+      for (int j = 0; j < NEQ; ++j) { const double t = tm.A(k, j); tm.A(k, j) = tm.A(p, j); tm.A(p, j) = t; }
+    const double inv = 1.0 / tm.A(k, k);
+    tm.at(OFF_INVD, k) = inv;
+    for (int i = k + 1; i < NEQ; ++i) {
+      const double l = tm.A(i, k) * inv;
+      tm.A(i, k) = l;
+      for (int j = k + 1; j < NEQ; ++j) tm.A(i, j) -= l * tm.A(k, j);
+    }
+  }
+#else
+  for (int k = 0; k < NEQ; ++k) {
+    // pivot search: (|a| key desc, row asc)
+    long long best = -1;
+    int p = NEQ;
+    for (int i = k + tm.tl; i < NEQ; i += TEAM) {
+      const long long v = abs_key(tm.A(i, k));
+      if (v > best) { best = v; p = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long vb = __shfl_xor_sync(0xffffffffu, best, o);
+      const int pb = __shfl_xor_sync(0xffffffffu, p, o);
+      if (vb > best || (vb == best && pb < p)) { best = vb; p = pb; }
+    }
+#if TEAM > 32
+    {
+      long long* rv = reinterpret_cast<long long*>(&tm.base[OFF_RED]);
+      int* ri = reinterpret_cast<int*>(&tm.base[OFF_RED + 8]);
+      if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = p; }
+      __syncthreads();
+      best = rv[0];
+      p = ri[0];
+      for (int w = 1; w < TEAM / 32; ++w)
+        if (rv[w] > best || (rv[w] == best && ri[w] < p)) { best = rv[w]; p = ri[w]; }
+      __syncthreads();
+    }
+#endif
+    if (p != k)
+      for (int j = tm.tl; j < NEQ; j += TEAM) { const double t = tm.A(k, j); tm.A(k, j) = tm.A(p, j); tm.A(p, j) = t; }
+    tsync();
+    const double inv = 1.0 / tm.A(k, k);
+    if (tm.tl == 0) { tm.piv(k) = p; tm.at(OFF_INVD, k) = inv; }
+    for (int i = k + 1 + tm.tl; i < NEQ; i += TEAM) tm.A(i, k) *= inv;
+    tsync();
+    const int m = NEQ - k - 1;
+    if (m > 0) {
+      const int tot = m * m;
+      const int qd = TEAM / m, rm = TEAM - qd * m;
+      int i = tm.tl / m, j = tm.tl - (tm.tl / m) * m;
+      for (int e = tm.tl; e < tot; e += TEAM) {
+        tm.A(k + 1 + i, k + 1 + j) -= tm.A(k + 1 + i, k) * tm.A(k, k + 1 + j);
+        i += qd;
+        j += rm;
+        if (j >= m) { j -= m; ++i; }
+      }
+    }
+    tsync();
+  }
+#endif
+}
+
+// Solve (LU) x = b in place on the vector at slot ob.  With TEAM > 1 only the first warp works.
+__device__ void lu_solve(const Team& tm, int ob) {
+#if TEAM == 1
+  for (int k = 0; k < NEQ; ++k) {
+    const int p = tm.piv(k);
+    if (p != k) { const double t = tm.at(ob, k); tm.at(ob, k) = tm.at(ob, p); tm.at(ob, p) = t; }
+  }
+  for (int i = 0; i < NEQ; ++i) {
+    double s = tm.at(ob, i);
+    for (int j = 0; j < i; ++j) s -= tm.A(i, j) * tm.at(ob, j);
+    tm.at(ob, i) = s;
+  }
+  for (int i = NEQ - 1; i >= 0; --i) {
+    double s = tm.at(ob, i);
+    for (int j = i + 1; j < NEQ; ++j) s -= tm.A(i, j) * tm.at(ob, j);
+    tm.at(ob, i) = s * tm.at(OFF_INVD, i);
+  }
+#else
+  if (tm.tl < 32) {
+    const int ln = tm.tl;
+    if (ln == 0)
+      for (int k = 0; k < NEQ; ++k) {
+        const int p = tm.piv(k);
+        if (p != k) { const double t = tm.at(ob, k); tm.at(ob, k) = tm.at(ob, p); tm.at(ob, p) = t; }
+      }
+    __syncwarp();
+    for (int k = 0; k < NEQ - 1; ++k) {
+      const double xk = tm.at(ob, k);
+      for (int i = k + 1 + ln; i < NEQ; i += 32) tm.at(ob, i) -= tm.A(i, k) * xk;
+      __syncwarp();
+    }
+    for (int k = NEQ - 1; k >= 0; --k) {
+      const double xk = tm.at(ob, k) * tm.at(OFF_INVD, k);
+      __syncwarp();
+      if (ln == (k & 31)) tm.at(ob, k) = xk;
+      for (int i = ln; i < k; i += 32) tm.at(ob, i) -= tm.A(i, k) * xk;
+      __syncwarp();
+    }
+  }
+  tsync();
+#endif
+}
+
+// ------------------------------------------------------------------------------ ROS4 step
+
+// Hairer-Wanner L-stable ROS4 in transformed variables (coefficients from the generated header:
+// RGAM, RA21, RA31, RA32, RC21, RC31, RC32, RC41, RC42, RC43, RM1..RM4, RE1..RE4; stage 4 is
+// evaluated at the same point as stage 3).
+// One attempt of size hh from y (OFF_Y): y_new into OFF_YT, returns the weighted RMS error
+// (infinity if anything is non-finite).
+__device__ double ros4_attempt(const Team& tm, double P, double hh, double rtol, double atol,
+                              const double* lnA_ext) {
+  const int U1 = OFF_U, U2 = OFF_U + NEQ, U3 = OFF_U + 2 * NEQ, U4 = OFF_U + 3 * NEQ;
+  // stage 1: f0 into U1, M = I/(gamma h) - J
+  eval_f_jac(tm, OFF_Y, U1, P, lnA_ext, -1.0, 1.0 / (RGAM * hh));
+  lu_factor(tm);
+  lu_solve(tm, U1);
+  const double ih = 1.0 / hh;
+  // stage 2
+  for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(OFF_YT, i) = tm.at(OFF_Y, i) + RA21 * tm.at(U1, i);
+  tsync();
+  eval_f(tm, OFF_YT, OFF_F, P, lnA_ext);
+  for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(U2, i) = tm.at(OFF_F, i) + (RC21 * ih) * tm.at(U1, i);
+  tsync();
+  lu_solve(tm, U2);
+  // stage 3 (and 4 at the same point)
+  for (int i = tm.tl; i < NEQ; i += TEAM)
+    tm.at(OFF_YT, i) = tm.at(OFF_Y, i) + RA31 * tm.at(U1, i) + RA32 * tm.at(U2, i);
+  tsync();
+  eval_f(tm, OFF_YT, OFF_F, P, lnA_ext);
+  for (int i = tm.tl; i < NEQ; i += TEAM)
+    tm.at(U3, i) = tm.at(OFF_F, i) + (RC31 * ih) * tm.at(U1, i) + (RC32 * ih) * tm.at(U2, i);
+  tsync();
+  lu_solve(tm, U3);
+  for (int i = tm.tl; i < NEQ; i += TEAM)
+    tm.at(U4, i) = tm.at(OFF_F, i) + (RC41 * ih) * tm.at(U1, i) + (RC42 * ih) * tm.at(U2, i) +
+                   (RC43 * ih) * tm.at(U3, i);
+  tsync();
+  lu_solve(tm, U4);
+  // new state, error estimate and its weighted RMS norm
+  double acc = 0.0;
+  bool bad = false;
+  for (int i = tm.tl; i < NEQ; i += TEAM) {
+    const double u1 = tm.at(U1, i), u2 = tm.at(U2, i), u3 = tm.at(U3, i), u4 = tm.at(U4, i);
+    const double y = tm.at(OFF_Y, i);
+    const double yn = y + RM1 * u1 + RM2 * u2 + RM3 * u3 + RM4 * u4;
+    const double e = RE1 * u1 + RE2 * u2 + RE3 * u3 + RE4 * u4;
+    tm.at(OFF_YT, i) = yn;
+    const double ay = fabs(y), an = fabs(yn);
+    const double sc = atol + rtol * (ay > an ? ay : an);
+    const double z = e / sc;
+    acc += z * z;
+    if (!isfinite(yn)) bad = true;
+  }
+  acc = team_sum(tm, acc);
+  bad = team_any(tm, bad);
+  tsync();
+  const double err = sqrt(acc / NEQ);
+  return (bad || !isfinite(err)) ? __longlong_as_double(0x7ff0000000000000LL) : err;
+}
+
+// Controller state of one cell (team-uniform: every lane holds the same values).
+struct Ctl {
+  double t, h;
+  int attempts, status;
+  bool reject_last, done;
+};
+
+// One attempt plus the controller decision (identical rules to the CPU oracle):
+// fac = clamp(0.9 err^-1/4, 0.2, 6) with err floored at 1e-10 (0.2 if non-finite); accept iff
+// err <= 1; no growth right after a rejection; the last step is cut to land on dt (a step
+// within 0.01% of the remainder is stretched to it); h_out is the controller's proposal after
+// the last accepted step, or the proposal that the end cut shortened.
+__device__ __forceinline__ void ros4_advance(const Team& tm, Ctl& c, double P, double dt, double rtol,
+                                             double atol, int max_steps, double h_min,
+                                             const double* lnA_ext) {
+  if (c.attempts >= max_steps) { c.status = ST_MAX_STEPS; c.done = true; return; }
+  if (c.h < h_min) { c.status = ST_H_UNDERFLOW; c.done = true; return; }
+  const bool last = c.t + 1.0001 * c.h >= dt;
+  const double hh = last ? dt - c.t : c.h;
+  const double err = ros4_attempt(tm, P, hh, rtol, atol, lnA_ext);
+  c.attempts++;
+  const bool finite = isfinite(err);
+  double fac = 0.2;
+  if (finite) {
+    const double e = err > 1e-10 ? err : 1e-10;
+    fac = 0.9 / sqrt(sqrt(e));
+    fac = fac < 0.2 ? 0.2 : (fac > 6.0 ? 6.0 : fac);
+  }
+  if (finite && err <= 1.0) {
+    for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(OFF_Y, i) = tm.at(OFF_YT, i);
+    tsync();
+    if (c.reject_last && fac > 1.0) fac = 1.0;
+    c.reject_last = false;
+    const double hnext = hh * fac;
+    if (last) {
+      c.h = hh < c.h ? c.h : hnext;
+      c.done = true;
+      c.status = ST_OK;
+      return;
+    }
+    c.t += hh;
+    c.h = hnext;
+  } else {
+    c.reject_last = true;
+    c.h = hh * fac;
+  }
+}
+
+// ------------------------------------------------------------------------------ cell I/O
+
+__device__ __forceinline__ Team make_team(double* smem) {
+  Team tm;
+#if TEAM == 1
+  tm.base = smem + threadIdx.x;
+  tm.tl = 0;
+#elif TEAM == 32
+  tm.base = smem + (threadIdx.x >> 5) * SLOTS;
+  tm.tl = threadIdx.x & 31;
+#else
+  tm.base = smem;
+  tm.tl = threadIdx.x;
+#endif
+  return tm;
+}
+
+// y = [T, Y_k / W_k] into OFF_Y; returns false if any input is non-finite
+__device__ __forceinline__ bool load_cell(const Team& tm, long long c, const double* T, const double* Y,
+                                          long long ld) {
+  bool bad = false;
+  if (tm.tl == 0) {
+    const double t = T[c];
+    tm.at(OFF_Y, 0) = t;
+    bad = !isfinite(t);
+  }
+  for (int k = tm.tl; k < NS - 1; k += TEAM) {
+    const double v = Y[k * ld + c];
+    tm.at(OFF_Y, 1 + k) = v * mk_invW[k];
+    bad = bad || !isfinite(v);
+  }
+  bad = team_any(tm, bad);
+  tsync();
+  return !bad;
+}
+
+// T, Y back from OFF_Y; the bath-gas mass fraction from the closure
+__device__ __forceinline__ void store_cell(const Team& tm, long long c, double* T, double* Y, long long ld) {
+  double s = 0.0;
+  for (int k = tm.tl; k < NS - 1; k += TEAM) {
+    const double v = tm.at(OFF_Y, 1 + k) * mk_W[k];
+    Y[k * ld + c] = v;
+    s += v;
+  }
+  s = team_sum(tm, s);
+  if (tm.tl == 0) {
+    T[c] = tm.at(OFF_Y, 0);
+    Y[(long long)(NS - 1) * ld + c] = 1.0 - s;
+  }
+}
+
+// broadcast a team-lane-0 value
+__device__ __forceinline__ long long team_bcast_ll(const Team& tm, long long v) {
+#if TEAM == 1
+  return v;
+#elif TEAM == 32
+  return __shfl_sync(0xffffffffu, v, 0);
+#else
+  long long* r = reinterpret_cast<long long*>(&tm.base[OFF_RED + 12]);
+  if (tm.tl == 0) *r = v;
+  __syncthreads();
+  v = *r;
+  __syncthreads();
+  return v;
+#endif
+}
+
+// ------------------------------------------------------------------------------ kernels
+
+extern "C" __global__ void __launch_bounds__(TPB)
+chem_eval_source_k(long long n_cells, const double* __restrict__ T, const double* __restrict__ P,
+                   const double* __restrict__ n, double* __restrict__ f, long long ld,
+                   const double* __restrict__ lnA_ext) {
+  extern __shared__ double smem[];
+  const Team tm = make_team(smem);
+  const long long team_id = (long long)blockIdx.x * NTEAM + (TEAM == 1 ? threadIdx.x : (TEAM == 32 ? threadIdx.x >> 5 : 0));
+  const long long stride = (long long)gridDim.x * NTEAM;
+  for (long long c = team_id; c < n_cells; c += stride) {
+    if (tm.tl == 0) tm.at(OFF_Y, 0) = T[c];
+    for (int k = tm.tl; k < NS - 1; k += TEAM) tm.at(OFF_Y, 1 + k) = n[k * ld + c];
+    tsync();
+    eval_f(tm, OFF_Y, OFF_F, P[c], lnA_ext);
+    for (int i = tm.tl; i < NEQ; i += TEAM) f[i * ld + c] = tm.at(OFF_F, i);
+    tsync();
+  }
+}
+
+extern "C" __global__ void __launch_bounds__(TPB)
+chem_eval_jacobian_k(long long n_cells, const double* __restrict__ T, const double* __restrict__ P,
+                     const double* __restrict__ n, double* __restrict__ J, long long ld,
+                     const double* __restrict__ lnA_ext) {
+  extern __shared__ double smem[];
+  const Team tm = make_team(smem);
+  const long long team_id = (long long)blockIdx.x * NTEAM + (TEAM == 1 ? threadIdx.x : (TEAM == 32 ? threadIdx.x >> 5 : 0));
+  const long long stride = (long long)gridDim.x * NTEAM;
+  for (long long c = team_id; c < n_cells; c += stride) {
+    if (tm.tl == 0) tm.at(OFF_Y, 0) = T[c];
+    for (int k = tm.tl; k < NS - 1; k += TEAM) tm.at(OFF_Y, 1 + k) = n[k * ld + c];
+    tsync();
+    eval_f_jac(tm, OFF_Y, OFF_F, P[c], lnA_ext, 1.0, 0.0);
+    for (int e = tm.tl; e < NEQ * NEQ; e += TEAM) J[(long long)e * ld + c] = tm.at(OFF_A, e);
+    tsync();
+  }
+}
+
+// Persistent driver: each team pulls cells from the queue counter and integrates them to dt.
+// With TEAM == 1 each thread refills independently (per-lane refill of retired cells); the
+// loop body is one step attempt so that lanes on different cells still execute it together.
+extern "C" __global__ void __launch_bounds__(TPB)
+chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __restrict__ P,
+                 double* __restrict__ Y, long long ld, double dt, double rtol, double atol,
+                 double* __restrict__ h_io, int* __restrict__ status_out,
+                 int* __restrict__ attempts_out, const double* __restrict__ lnA_ext,
+                 int max_steps, double h_min, double T_min, unsigned long long* queue) {
+  extern __shared__ double smem[];
+  const Team tm = make_team(smem);
+  long long cell = -1;
+  double Pc = 0.0;
+  Ctl c;
+  c.done = true;
+  // bounded: every iteration either retires a cell or makes an attempt (<= max_steps per cell)
+  for (;;) {
+    if (c.done) {
+      long long nc = 0;
+      if (tm.tl == 0) nc = (long long)atomicAdd(queue, 1ULL);
+      cell = team_bcast_ll(tm, nc);
+      if (cell >= n_cells) break;
+      Pc = P[cell];
+      c.t = 0.0;
+      c.h = h_io ? h_io[cell] : 0.0;
+      if (!(c.h > 0.0)) c.h = dt;
+      c.attempts = 0;
+      c.status = ST_OK;
+      c.reject_last = false;
+      c.done = false;
+      const bool ok = load_cell(tm, cell, T, Y, ld);
+      if (!ok || tm.at(OFF_Y, 0) < T_min) {
+        if (tm.tl == 0) {
+          if (status_out) status_out[cell] = ok ? ST_SKIPPED : ST_NONFINITE;
+          if (attempts_out) attempts_out[cell] = 0;
+        }
+        c.done = true;
+        tsync();
+        continue;
+      }
+    }
+    ros4_advance(tm, c, Pc, dt, rtol, atol, max_steps, h_min, lnA_ext);
+    if (c.done) {
+      store_cell(tm, cell, T, Y, ld);
+      if (tm.tl == 0) {
+        if (h_io) h_io[cell] = c.h;
+        if (status_out) status_out[cell] = c.status;
+        if (attempts_out) attempts_out[cell] = c.attempts;
+      }
+      tsync();
+    }
+  }
+}
+
+// Plain driver, one launch per step attempt over all cells.  Per-cell controller state lives
+// in the workspace: y [NEQ][n] (cell-fastest), t, h [n], packed flags/attempts/status [n].
+struct PlainWs {
+  double* y;
+  double* t;
+  double* h;
+  int* flags;     // bit0 active, bit1 reject_last
+  int* attempts;
+  int* status;
+  unsigned int* active_count;  // one counter per launch index
+};
+
+extern "C" __global__ void __launch_bounds__(TPB)
+chem_plain_init_k(long long n_cells, const double* __restrict__ T, const double* __restrict__ Y,
+                  long long ld, double dt, const double* __restrict__ h_in, double T_min,
+                  double* wy, double* wt, double* wh, int* wflags, int* watt, int* wst) {
+  extern __shared__ double smem[];
+  const Team tm = make_team(smem);
+  const long long team_id = (long long)blockIdx.x * NTEAM + (TEAM == 1 ? threadIdx.x : (TEAM == 32 ? threadIdx.x >> 5 : 0));
+  const long long stride = (long long)gridDim.x * NTEAM;
+  for (long long c = team_id; c < n_cells; c += stride) {
+    const bool ok = load_cell(tm, c, T, Y, ld);
+    for (int i = tm.tl; i < NEQ; i += TEAM) wy[i * n_cells + c] = tm.at(OFF_Y, i);
+    if (tm.tl == 0) {
+      double h = h_in ? h_in[c] : 0.0;
+      if (!(h > 0.0)) h = dt;
+      wt[c] = 0.0;
+      wh[c] = h;
+      watt[c] = 0;
+      const bool skip = ok && tm.at(OFF_Y, 0) < T_min;
+      wst[c] = ok ? (skip ? ST_SKIPPED : ST_OK) : ST_NONFINITE;
+      wflags[c] = (ok && !skip) ? 1 : 0;
+    }
+    tsync();
+  }
+}
+
+extern "C" __global__ void __launch_bounds__(TPB)
+chem_plain_attempt_k(long long n_cells, double* __restrict__ T, const double* __restrict__ P,
+                     double* __restrict__ Y, long long ld, double dt, double rtol, double atol,
+                     double* __restrict__ h_out, int* __restrict__ status_out,
+                     int* __restrict__ attempts_out, const double* __restrict__ lnA_ext,
+                     int max_steps, double h_min, double* wy, double* wt, double* wh, int* wflags,
+                     int* watt, int* wst, unsigned int* active_count) {
+  extern __shared__ double smem[];
+  const Team tm = make_team(smem);
+  const long long team_id = (long long)blockIdx.x * NTEAM + (TEAM == 1 ? threadIdx.x : (TEAM == 32 ? threadIdx.x >> 5 : 0));
+  const long long stride = (long long)gridDim.x * NTEAM;
+  for (long long cell = team_id; cell < n_cells; cell += stride) {
+    const int fl = wflags[cell];
+    if (!(fl & 1)) continue;  // team-uniform
+    for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(OFF_Y, i) = wy[i * n_cells + cell];
+    tsync();
+    Ctl c;
+    c.t = wt[cell];
+    c.h = wh[cell];
+    c.attempts = watt[cell];
+    c.status = ST_OK;
+    c.reject_last = (fl & 2) != 0;
+    c.done = false;
+    ros4_advance(tm, c, P[cell], dt, rtol, atol, max_steps, h_min, lnA_ext);
+    if (c.done) {
+      store_cell(tm, cell, T, Y, ld);
+      if (tm.tl == 0) {
+        if (h_out) h_out[cell] = c.h;
+        if (status_out) status_out[cell] = c.status;
+        if (attempts_out) attempts_out[cell] = c.attempts;
+        wflags[cell] = 0;
+      }
+    } else {
+      for (int i = tm.tl; i < NEQ; i += TEAM) wy[i * n_cells + cell] = tm.at(OFF_Y, i);
+      if (tm.tl == 0) {
+        wt[cell] = c.t;
+        wh[cell] = c.h;
+        watt[cell] = c.attempts;
+        wflags[cell] = 1 | (c.reject_last ? 2 : 0);
+        atomicAdd(active_count, 1u);
+      }
+    }
+    tsync();
+  }
+}
+
+// Cells the plain driver never activated (non-finite or below T_min) get their status here.
+extern "C" __global__ void chem_plain_finish_k(long long n_cells, int* __restrict__ status_out,
+                                               int* __restrict__ attempts_out, const int* wst,
+                                               const int* wflags_init_status) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const int s = wst[c];
+  if (s == ST_SKIPPED || s == ST_NONFINITE) {
+    if (status_out) status_out[c] = s;
+    if (attempts_out) attempts_out[c] = 0;
+  }
+  (void)wflags_init_status;
+}

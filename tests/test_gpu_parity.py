@@ -1,0 +1,257 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on the same seeded inputs.
+
+Tolerances (stated, from the problem statement's bounds):
+  * source terms and Jacobian: |x - x_oracle| <= 1e-12 (|x_oracle| + g), where g is the gross
+    magnitude of the row (sum of |forward| + |reverse| contributions for f; the largest entry of
+    the row for J), because near equilibrium net rates cancel;
+  * integrated states: the weighted RMS norm of Eq. (e:ivp_norm), with the solver's rtol=1e-6
+    and atol=1e-10 as weights, <= 1e-5 per cell, for cells whose accepted/rejected step
+    sequence matches the oracle's (identical attempt counts); cells where round-off flipped an
+    accept/reject decision (allowed in at most 2% of cells) must lie within 10 tolerance units
+    of a tight (rtol 1e-10) oracle solution, i.e. be as valid a rtol=1e-6 solution as the
+    oracle's own.
+"""
+import numpy as np
+import pytest
+
+from tests.conftest import states
+from tests.gpu_helpers import gpu_mech, gpu_state, gross_f, to_dev, weighted_norm
+
+pytestmark = pytest.mark.gpu
+
+WORK = {"h2_13": "h2_fresh", "ch4_53": "ch4_partial", "ch4_111": "ch4_front"}
+CONFIGS = {
+    "h2_13": [(1, 32), (32, 64), (32, 128), (64, 64), (128, 128)],
+    "ch4_53": [(32, 32), (32, 64), (64, 64), (128, 128), (256, 256)],
+    "ch4_111": [(32, 32), (128, 128), (256, 256)],
+}
+PARAMS = [(n, t, b) for n in CONFIGS for (t, b) in CONFIGS[n]]
+
+
+@pytest.fixture(scope="module")
+def gmech(mech_path):
+    cache = {}
+
+    def get(name, team, block):
+        key = (name, team, block)
+        if key not in cache:
+            cache[key] = gpu_mech(mech_path(name), team=team, block=block)
+        return cache[key]
+
+    return get
+
+
+def _inputs(om, name, n, seed):
+    st = states(name, n, WORK[name], seed)
+    y = om.state_from_TY(st.T, st.Y)
+    return st, y
+
+
+@pytest.mark.parametrize("name,team,block", PARAMS)
+def test_eval_source_parity(omech, gmech, name, team, block):
+    om = omech(name)
+    g = gmech(name, team, block)
+    n = {"h2_13": 1000, "ch4_53": 300, "ch4_111": 100}[name]
+    st, y = _inputs(om, name, n, 101)
+    f = g.eval_source(to_dev(y[:, 0]), to_dev(st.P), to_dev(y[:, 1:].T)).cpu().numpy().T
+    fo = om.source(y, st.P)
+    for c in range(n):
+        gr = gross_f(om, y[c], st.P[c])
+        err = np.abs(f[c] - fo[c]) / (np.abs(fo[c]) + gr + 1e-300)
+        assert err.max() <= 1e-12, (c, err.max(), np.argmax(err))
+
+
+@pytest.mark.parametrize("name,team,block", PARAMS)
+def test_eval_jacobian_parity(omech, gmech, name, team, block):
+    om = omech(name)
+    g = gmech(name, team, block)
+    n = {"h2_13": 200, "ch4_53": 40, "ch4_111": 12}[name]
+    st, y = _inputs(om, name, n, 102)
+    J = g.eval_jacobian(to_dev(y[:, 0]), to_dev(st.P), to_dev(y[:, 1:].T)).cpu().numpy().T
+    J = J.reshape(n, om.N, om.N)
+    Jo = om.jacobian(y, st.P, threads=16)
+    for c in range(n):
+        rowmax = np.abs(Jo[c]).max(axis=1, keepdims=True)
+        err = np.abs(J[c] - Jo[c]) / (np.abs(Jo[c]) + rowmax + 1e-300)
+        assert err.max() <= 1e-12, (c, err.max(), np.unravel_index(np.argmax(err), err.shape))
+
+
+def _check_integration(om, st, y0, yg, info_att, dt, label):
+    yo, info = om.integrate(y0, st.P, dt, threads=16)
+    assert np.all(info["status"] == 0)
+    same = info["attempts"] == info_att
+    e = weighted_norm(yo, yg)
+    assert np.all(e[same] <= 1e-5), (label, e[same].max(), np.argmax(np.where(same, e, 0)))
+    flips = np.where(~same)[0]
+    assert len(flips) <= max(1, int(0.02 * len(same))), (label, len(flips))
+    if len(flips):
+        yt, it = om.integrate(y0[flips], st.P[flips], dt, rtol=1e-10, atol=1e-14, threads=16)
+        assert np.all(weighted_norm(yt, yg[flips]) <= 10.0), label
+    return e, len(flips)
+
+
+@pytest.mark.parametrize("name,team,block", PARAMS)
+def test_integrate_parity(omech, gmech, name, team, block):
+    import torch
+    om = omech(name)
+    g = gmech(name, team, block)
+    n = {"h2_13": 777, "ch4_53": 150, "ch4_111": 40}[name]
+    st, y0 = _inputs(om, name, n, 103)
+    T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    status = torch.full((n,), -1, dtype=torch.int32, device=T.device)
+    att = torch.zeros(n, dtype=torch.int32, device=T.device)
+    h = torch.zeros(n, dtype=torch.float64, device=T.device)
+    g.integrate(T, P, Y, 1e-6, h=h, status=status, opts=g.opts(attempts=att))
+    assert (status.cpu().numpy() == 0).all()
+    yg = gpu_state(om, T, Y)
+    _check_integration(om, st, y0, yg, att.cpu().numpy(), 1e-6, (name, team, block))
+    # mass closure written back: sum Y = 1
+    assert np.abs(Y.sum(0).cpu().numpy() - 1.0).max() < 1e-13
+    assert (h.cpu().numpy() > 0).all()
+
+
+@pytest.mark.parametrize("name", ["h2_13", "ch4_53"])
+def test_plain_driver_matches_persistent(omech, gmech, name):
+    """The one-launch-per-attempt driver runs the same per-cell arithmetic: bitwise equal."""
+    import torch
+    from paper_2205_05681_gb300 import chem
+    om = omech(name)
+    team, block = CONFIGS[name][1]
+    g = gmech(name, team, block)
+    n = 300
+    st, y0 = _inputs(om, name, n, 104)
+    outs = []
+    for mode in (chem.MODE_PERSISTENT, chem.MODE_PLAIN):
+        T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+        h = torch.zeros(n, dtype=torch.float64, device=T.device)
+        st_ = torch.full((n,), -1, dtype=torch.int32, device=T.device)
+        att = torch.zeros(n, dtype=torch.int32, device=T.device)
+        o = g.opts(mode=mode, attempts=att)
+        g.integrate(T, P, Y, 1e-6, h=h, status=st_, opts=o)
+        outs.append([x.cpu().numpy() for x in (T, Y, h, st_, att)])
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+def test_full_size_sampled_53(omech, gmech):
+    """65,536 cells of the 53-species workload in the launch configuration the bench times;
+    a sample of cells against the oracle one by one."""
+    import torch
+    name = "ch4_53"
+    om = omech(name)
+    team, block = CONFIGS[name][1]
+    g = gmech(name, team, block)
+    n = 65536
+    st = states(name, n, WORK[name], 8)
+    T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    att = torch.zeros(n, dtype=torch.int32, device=T.device)
+    status = torch.full((n,), -1, dtype=torch.int32, device=T.device)
+    g.integrate(T, P, Y, 1e-6, status=status, opts=g.opts(attempts=att))
+    assert (status.cpu().numpy() == 0).all()
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(n, 48, replace=False))
+    idx[-1] = n - 1  # the ragged tail of the last block
+    yg = gpu_state(om, T, Y)[idx]
+    y0 = om.state_from_TY(st.T[idx], st.Y[idx])
+
+    class Sub:
+        P = st.P[idx]
+
+    _check_integration(om, Sub, y0, yg, att.cpu().numpy()[idx], 1e-6, "full53")
+
+
+def test_edge_cases(omech, gmech):
+    import torch
+    from paper_2205_05681_gb300 import chem
+    name = "h2_13"
+    om = omech(name)
+    g = gmech(name, 32, 64)
+    dev = torch.device("cuda:0")
+    # empty batch: a no-op
+    e = torch.zeros(0, dtype=torch.float64, device=dev)
+    g.integrate(e, e, torch.zeros((om.ns, 0), dtype=torch.float64, device=dev), 1e-6)
+    st, y0 = _inputs(om, name, 5, 105)
+    T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    T[1] = float("nan")
+    T[2] = 200.0  # below T_min
+    T0, Y0 = T.clone(), Y.clone()
+    status = torch.full((5,), -1, dtype=torch.int32, device=dev)
+    att = torch.full((5,), -1, dtype=torch.int32, device=dev)
+    g.integrate(T, P, Y, 1e-6, status=status, opts=g.opts(T_min=300.0, attempts=att))
+    s = status.cpu().numpy()
+    assert s[1] == chem.STATUS_NONFINITE and s[2] == chem.STATUS_SKIPPED
+    assert s[0] == 0 and s[3] == 0 and s[4] == 0
+    assert att.cpu().numpy()[1] == 0 and att.cpu().numpy()[2] == 0
+    assert torch.equal(Y[:, 2], Y0[:, 2]) and T[2].item() == 200.0
+    # max_steps and h_min failures are reported per cell
+    T, Y = to_dev(st.T), to_dev(st.Y.T)
+    status.fill_(-1)
+    g.integrate(T, P, Y, 1e-3, status=status, opts=g.opts(max_steps=2, attempts=att))
+    assert (status.cpu().numpy() == chem.STATUS_MAX_STEPS).all()
+    assert (att.cpu().numpy() == 2).all()
+    T, Y = to_dev(st.T), to_dev(st.Y.T)
+    g.integrate(T, P, Y, 1e-6, status=status, opts=g.opts(h_min=1.0))
+    assert (status.cpu().numpy() == chem.STATUS_H_UNDERFLOW).all()
+    # a single cell, and bad arguments raise instead of launching
+    st1, y1 = _inputs(om, name, 1, 106)
+    T, P, Y = to_dev(st1.T), to_dev(st1.P), to_dev(st1.Y.T)
+    g.integrate(T, P, Y, 1e-6)
+    yo, _ = om.integrate(y1, st1.P, 1e-6)
+    assert weighted_norm(yo, gpu_state(om, T, Y)).max() <= 1e-5
+    with pytest.raises(chem.ChemError):
+        g.integrate(T, P, Y, -1.0)
+    with pytest.raises(chem.ChemError):
+        g.integrate(T, P, Y, 1e-6, workspace=torch.zeros(8, dtype=torch.uint8, device=dev))
+
+
+def test_lnA_override(omech, gmech):
+    """The ln A parameters passed at run time replace the built-in ones in f and in the step."""
+    name = "h2_13"
+    om = omech(name)
+    g = gmech(name, 32, 64)
+    rng = np.random.default_rng(7)
+    lnA = om.lnA + rng.normal(0.0, 0.3, om.nr)
+    st, y = _inputs(om, name, 64, 107)
+    f = g.eval_source(to_dev(y[:, 0]), to_dev(st.P), to_dev(y[:, 1:].T), lnA=to_dev(lnA))
+    fo = om.source(y, st.P, lnA=lnA)
+    assert np.allclose(f.cpu().numpy().T, fo, rtol=1e-11, atol=1e-11 * np.abs(fo).max())
+    assert np.array_equal(g.lnA(), om.lnA) or np.allclose(g.lnA(), om.lnA, rtol=1e-15, atol=0)
+    T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    g.integrate(T, P, Y, 1e-6, opts=g.opts(lnA=to_dev(lnA)))
+    yo, _ = om.integrate(y, st.P, 1e-6, lnA=lnA)
+    assert weighted_norm(yo, gpu_state(om, T, Y)).max() <= 1e-5
+
+
+def test_host_entry_point(omech, gmech):
+    """chem_integrate_host: host arrays in, host arrays out."""
+    name = "ch4_53"
+    om = omech(name)
+    g = gmech(name, 32, 64)
+    st, y0 = _inputs(om, name, 64, 108)
+    T = st.T.copy()
+    Y = np.ascontiguousarray(st.Y.T)
+    h = np.zeros(64)
+    status = np.full(64, -1, dtype=np.int32)
+    g.integrate_host(T, np.ascontiguousarray(st.P), Y, 1e-6, h=h, status=status)
+    assert (status == 0).all() and (h > 0).all()
+    yo, _ = om.integrate(y0, st.P, 1e-6, threads=16)
+    assert weighted_norm(yo, om.state_from_TY(T, Y.T)).max() <= 1e-5
+
+
+def test_h_carries_across_split_steps(omech, gmech):
+    """h_out of one call is the first step of the next (BatchedChemistryModel reuse)."""
+    import torch
+    name = "h2_13"
+    om = omech(name)
+    g = gmech(name, 32, 64)
+    st, y0 = _inputs(om, name, 128, 109)
+    T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    h = torch.zeros(128, dtype=torch.float64, device=T.device)
+    y = y0.copy()
+    hh = np.zeros(128)
+    for _ in range(3):
+        g.integrate(T, P, Y, 1e-6, h=h)
+        y, info = om.integrate(y, st.P, 1e-6, h=hh)
+        hh = info["h"]
+    assert weighted_norm(y, gpu_state(om, T, Y)).max() <= 1e-5
+    assert np.allclose(h.cpu().numpy(), hh, rtol=1e-6)
