@@ -223,6 +223,9 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-kernel comparison")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--cells", type=int, default=0,
+                    help="use only the first CELLS cells of the workload (small profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -243,6 +246,9 @@ def main():
     m = chem.Mechanism(path, team=args.team, block=args.block)
     load_s = time.perf_counter() - t0
     st = synth.make_states(synth.mechanism(mech_name), n_cells, recipe, seed)
+    if args.cells:
+        n_cells = min(n_cells, args.cells)
+        st = synth.States(st.T[:n_cells], st.P[:n_cells], st.Y[:n_cells])
     T0 = torch.tensor(st.T, device=dev)
     P = torch.tensor(st.P, device=dev)
     Y0 = torch.tensor(np.ascontiguousarray(st.Y.T), device=dev)
@@ -300,7 +306,7 @@ def main():
     hh = np.zeros(n_cells)
     sh = np.zeros(n_cells, dtype=np.int32)
     e2e_t = []
-    for i in range(max(1, min(args.steps, 3)) + 1):
+    for i in range(0 if args.no_e2e else max(1, min(args.steps, 3)) + 1):
         Th[:] = st.T
         Yh[:] = st.Y.T
         hh[:] = 0
@@ -310,7 +316,7 @@ def main():
         el = time.perf_counter() - t0
         if i:
             e2e_t.append(el)
-    e2e_sec = statistics.median(e2e_t)
+    e2e_sec = statistics.median(e2e_t) if e2e_t else float("nan")
 
     # plain one-launch-per-attempt kernel on the same inputs
     plain = None

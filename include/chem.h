@@ -67,6 +67,7 @@ typedef struct {
   int32_t block;       /* threads per block; 0 = chosen with team */
   int32_t verbose;     /* print compile logs (register use) to stderr */
   const char* cache_dir; /* directory for compiled cubins; NULL = no disk cache */
+  int32_t adjoint;     /* chem_mech_compile_only: compile the adjoint module instead */
 } chem_build_opts;
 
 /* Options for chem_integrate (NULL = defaults shown). */
@@ -140,6 +141,70 @@ int chem_integrate(chem_mech_t mech, int64_t n_cells, double* T, const double* P
 int chem_integrate_host(chem_mech_t mech, int64_t n_cells, double* T, const double* P,
                         double* Y, double dt, double rtol, double atol, double* h,
                         int32_t* status, const chem_int_opts* opts, void* stream);
+
+/* ---- discrete adjoint (gradients of a loss on the final state) -------------------------
+ * The forward is differentiated as the discrete map it is: the ROS4 steps of Sec. 2.3 with the
+ * accepted step sizes frozen.  chem_integrate_ckpt records, per cell, every accepted step size
+ * and the state after every `interval` accepted steps ("checkpoints"); chem_adjoint walks the
+ * checkpoints backwards, recomputes the states between them, and pulls the loss gradient back
+ * through each step's stages, LU and Jacobian (second derivatives of f by dual numbers).
+ * (The paper has no adjoint; this extends its integrator.) */
+
+/* Caller-owned device memory for one checkpointed forward. */
+typedef struct {
+  void* mem;          /* device, 256-byte aligned, >= chem_tape_bytes(...) */
+  size_t bytes;
+  int64_t n_cells;
+  int32_t capacity;   /* accepted steps per cell the tape can hold */
+  int32_t interval;   /* checkpoint every `interval` accepted steps (>= 1) */
+} chem_tape;
+
+/* Bytes of a tape: per cell an int (accepted count), capacity step sizes and
+ * ((capacity-1)/interval + 1) checkpoint states of Ns doubles. */
+size_t chem_tape_bytes(chem_mech_t mech, int64_t n_cells, int32_t capacity, int32_t interval);
+
+/* chem_integrate (persistent driver) that also records the tape.  A cell that accepts more
+ * than `capacity` steps stops with status CHEM_STATUS_TAPE_FULL.  workspace: >= 256 bytes. */
+#define CHEM_STATUS_TAPE_FULL 5
+int chem_integrate_ckpt(chem_mech_t mech, int64_t n_cells, double* T, const double* P, double* Y,
+                        int64_t ld, double dt, double rtol, double atol, double* h,
+                        int32_t* status, const chem_int_opts* opts, const chem_tape* tape,
+                        void* workspace, size_t ws_bytes, void* stream);
+
+/* Device workspace of chem_adjoint (the recomputed segment states of every team in flight and
+ * per-team partial gradients). */
+size_t chem_adjoint_workspace(chem_mech_t mech, int64_t n_cells, const chem_int_opts* opts,
+                              int32_t interval);
+
+/* Reverse sweep.  Inputs: P [n_cells]; gT [n_cells] = dL/dT_final; gY [Ns x ld] = dL/dY_final
+ * (mass fractions, all Ns species); the tape of the matching chem_integrate_ckpt call; opts->lnA
+ * the same parameters as the forward (NULL = built-in).  Outputs: g_lnA [Nr] = dL/d lnA summed
+ * over cells (a fixed-order reduction, deterministic); gT0 [n_cells] = dL/dT_0; gY0 [Ns x ld] =
+ * dL/dY_0 (the state carries n_k = Y_k/W_k for k < Ns, so the bath-gas entry is 0).  Needs a
+ * multi-lane kernel configuration (team >= 32). */
+int chem_adjoint(chem_mech_t mech, int64_t n_cells, const double* P, const double* gT,
+                 const double* gY, int64_t ld, const chem_tape* tape, const chem_int_opts* opts,
+                 double* g_lnA, double* gT0, double* gY0, void* workspace, size_t ws_bytes,
+                 void* stream);
+
+/* Vector-Jacobian products of f (Eq. e:jac transposed), the adjoint's building block, per cell:
+ * gy [Ns x ld] = J(y)^T v and gp [Nr x ld] = (d f / d lnA)^T v, for v [Ns x ld] on the state
+ * rows.  T, P, n as in chem_eval_source. */
+int chem_eval_vjp(chem_mech_t mech, int64_t n_cells, const double* T, const double* P,
+                  const double* n, const double* v, double* gy, double* gp, int64_t ld,
+                  const double* lnA, void* stream);
+
+/* Autotuner: picks the fastest kernel configuration (lanes per cell "team" and threads per
+ * block) for this mechanism by integrating a sample of the caller's cells (the first
+ * min(n_cells, 4096) of T, P, Y [Ns x ld]) once per candidate configuration that fits in shared
+ * memory, and makes it the mechanism's default.  The caller's arrays are not modified (the sample
+ * is copied).  Candidate modules are compiled on first use (NVRTC; cached in cache_dir).
+ * Set-up time only: allocates temporary device memory and synchronises `stream`.  Outputs
+ * (nullable): the chosen team and block and the sample's integration time in ms.
+ * (Not from the paper, which tunes nothing at run time: its vector width is fixed at 8.) */
+int chem_autotune(chem_mech_t mech, int64_t n_cells, const double* T, const double* P,
+                  const double* Y, int64_t ld, double dt, double rtol, double atol, void* stream,
+                  int32_t* team, int32_t* block, float* ms);
 
 /* Kernel configuration actually used by chem_integrate for these options (team, block,
  * dynamic shared memory bytes, registers per thread); for reports. */

@@ -22,14 +22,22 @@ STATUS_OK, STATUS_MAX_STEPS, STATUS_H_UNDERFLOW, STATUS_NONFINITE, STATUS_SKIPPE
 
 EXPORTS = ["chem_mech_load", "chem_mech_compile_only", "chem_mech_free", "chem_mech_info",
            "chem_mech_lnA", "chem_eval_source", "chem_eval_jacobian", "chem_integrate_workspace",
-           "chem_integrate", "chem_integrate_host", "chem_kernel_config", "chem_last_error"]
+           "chem_integrate", "chem_integrate_host", "chem_kernel_config", "chem_autotune",
+           "chem_tape_bytes", "chem_integrate_ckpt", "chem_adjoint_workspace", "chem_adjoint",
+           "chem_eval_vjp", "chem_last_error"]
+STATUS_TAPE_FULL = 5
 
 CACHE_DIR = os.environ.get("CHEM_CACHE_DIR", os.path.join(os.path.dirname(__file__), "_cache"))
 
 
 class BuildOpts(C.Structure):
     _fields_ = [("team", C.c_int32), ("block", C.c_int32), ("verbose", C.c_int32),
-                ("cache_dir", C.c_char_p)]
+                ("cache_dir", C.c_char_p), ("adjoint", C.c_int32)]
+
+
+class TapeStruct(C.Structure):
+    _fields_ = [("mem", C.c_void_p), ("bytes", C.c_size_t), ("n_cells", C.c_int64),
+                ("capacity", C.c_int32), ("interval", C.c_int32)]
 
 
 class IntOpts(C.Structure):
@@ -74,6 +82,19 @@ def library(build_if_missing: bool = True):
             lib.chem_integrate_host.argtypes = [vp, i64, vp, vp, vp, dbl, dbl, dbl, vp, vp,
                                                 C.POINTER(IntOpts), vp]
             lib.chem_kernel_config.argtypes = [vp, C.POINTER(IntOpts)] + [C.POINTER(C.c_int32)] * 4
+            lib.chem_tape_bytes.restype = C.c_size_t
+            lib.chem_tape_bytes.argtypes = [vp, i64, C.c_int32, C.c_int32]
+            lib.chem_integrate_ckpt.argtypes = [vp, i64, vp, vp, vp, i64, dbl, dbl, dbl, vp, vp,
+                                                C.POINTER(IntOpts), C.POINTER(TapeStruct), vp,
+                                                C.c_size_t, vp]
+            lib.chem_adjoint_workspace.restype = C.c_size_t
+            lib.chem_adjoint_workspace.argtypes = [vp, i64, C.POINTER(IntOpts), C.c_int32]
+            lib.chem_adjoint.argtypes = [vp, i64, vp, vp, vp, i64, C.POINTER(TapeStruct),
+                                         C.POINTER(IntOpts), vp, vp, vp, vp, C.c_size_t, vp]
+            lib.chem_eval_vjp.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i64, vp, vp]
+            lib.chem_autotune.argtypes = [vp, i64, vp, vp, vp, i64, dbl, dbl, dbl, vp,
+                                          C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_float)]
             _lib = lib
     return _lib
 
@@ -84,10 +105,11 @@ def _check(rc: int):
 
 
 def compile_only(spec_path: str, team: int = 0, block: int = 0, cache_dir: Optional[str] = None,
-                 verbose: bool = False) -> str:
+                 verbose: bool = False, adjoint: bool = False) -> str:
     """Generate and NVRTC-compile a mechanism's kernels for sm_103a (no GPU needed)."""
     buf = C.create_string_buffer(1 << 16)
-    o = BuildOpts(team, block, int(verbose), cache_dir.encode() if cache_dir else None)
+    o = BuildOpts(team, block, int(verbose), cache_dir.encode() if cache_dir else None,
+                  int(adjoint))
     _check(library().chem_mech_compile_only(spec_path.encode(), C.byref(o), buf, len(buf)))
     return buf.value.decode(errors="replace")
 
@@ -127,7 +149,7 @@ class Mechanism:
         self._lib = lib
         self.spec_path = spec_path
         h = C.c_void_p()
-        o = BuildOpts(team, block, int(verbose), cache_dir.encode() if cache_dir else None)
+        o = BuildOpts(team, block, int(verbose), cache_dir.encode() if cache_dir else None, 0)
         _check(lib.chem_mech_load(spec_path.encode(), C.byref(o), C.byref(h)))
         self._h = h
         ns, nr, ne = C.c_int32(), C.c_int32(), C.c_int32()
@@ -224,9 +246,120 @@ class Mechanism:
                                              Y.ctypes.data_as(C.c_void_p), dt, rtol, atol, hp, sp,
                                              C.byref(o), _stream(stream)))
 
+    # ------------------------------------------------------------------ adjoint
+    def make_tape(self, n_cells: int, capacity: int = 2048, interval: int = 16, device="cuda"):
+        """Device memory for one checkpointed forward (see chem_tape_bytes)."""
+        import torch
+        nbytes = int(self._lib.chem_tape_bytes(self._h, n_cells, capacity, interval))
+        if nbytes == 0:
+            raise ChemError("bad tape sizes")
+        buf = torch.empty((nbytes + 255) // 256 * 256, dtype=torch.uint8, device=device)
+        return Tape(buf, n_cells, capacity, interval)
+
+    def integrate_ckpt(self, T, P, Y, dt, tape, rtol=1e-6, atol=1e-10, h=None, status=None,
+                       opts=None, workspace=None, stream=None):
+        """chem_integrate that records `tape` for chem_adjoint (in place on T, Y)."""
+        import torch
+        Cn = T.shape[0]
+        _req(T, "T", shape=(Cn,)); _req(P, "P", shape=(Cn,)); _req(Y, "Y", shape=(self.ns, Cn))
+        o = opts or self.opts()
+        if workspace is None:
+            workspace = torch.empty(256, dtype=torch.uint8, device=T.device)
+        _check(self._lib.chem_integrate_ckpt(self._h, Cn, _ptr(T), _ptr(P), _ptr(Y), Cn, dt, rtol,
+                                             atol, _ptr(h), _ptr(status), C.byref(o),
+                                             C.byref(tape.struct), _ptr(workspace),
+                                             workspace.numel(), _stream(stream)))
+        return T, Y
+
+    def adjoint(self, P, gT, gY, tape, opts=None, stream=None):
+        """Reverse sweep: returns (g_lnA [Nr], gT0 [C], gY0 [Ns, C])."""
+        import torch
+        Cn = P.shape[0]
+        _req(P, "P", shape=(Cn,)); _req(gT, "gT", shape=(Cn,)); _req(gY, "gY", shape=(self.ns, Cn))
+        o = opts or self.opts()
+        nb = int(self._lib.chem_adjoint_workspace(self._h, Cn, C.byref(o), tape.interval))
+        if nb == 0:
+            _check(-1)
+        ws = torch.empty((nb + 255) // 256 * 256, dtype=torch.uint8, device=P.device)
+        g_lnA = torch.empty(self.nr, dtype=torch.float64, device=P.device)
+        gT0 = torch.empty(Cn, dtype=torch.float64, device=P.device)
+        gY0 = torch.empty((self.ns, Cn), dtype=torch.float64, device=P.device)
+        _check(self._lib.chem_adjoint(self._h, Cn, _ptr(P), _ptr(gT), _ptr(gY), Cn,
+                                      C.byref(tape.struct), C.byref(o), _ptr(g_lnA), _ptr(gT0),
+                                      _ptr(gY0), _ptr(ws), ws.numel(), _stream(stream)))
+        return g_lnA, gT0, gY0
+
+    def eval_vjp(self, T, P, n, v, lnA=None, stream=None):
+        """gy = J^T v [Ns, C] and gp = (df/dlnA)^T v [Nr, C] per cell."""
+        import torch
+        Cn = T.shape[0]
+        _req(T, "T", shape=(Cn,)); _req(P, "P", shape=(Cn,)); _req(n, "n", shape=(self.ns - 1, Cn))
+        _req(v, "v", shape=(self.ns, Cn))
+        gy = torch.empty((self.ns, Cn), dtype=torch.float64, device=T.device)
+        gp = torch.empty((self.nr, Cn), dtype=torch.float64, device=T.device)
+        _check(self._lib.chem_eval_vjp(self._h, Cn, _ptr(T), _ptr(P), _ptr(n), _ptr(v), _ptr(gy),
+                                       _ptr(gp), Cn, _ptr(lnA), _stream(stream)))
+        return gy, gp
+
+    def autotune(self, T, P, Y, dt, rtol=1e-6, atol=1e-10, stream=None):
+        """Choose and set the fastest (team, block) on a sample of these cells; returns it."""
+        Cn = T.shape[0]
+        _req(T, "T", shape=(Cn,)); _req(P, "P", shape=(Cn,)); _req(Y, "Y", shape=(self.ns, Cn))
+        t, b, ms = C.c_int32(), C.c_int32(), C.c_float()
+        _check(self._lib.chem_autotune(self._h, Cn, _ptr(T), _ptr(P), _ptr(Y), Cn, dt, rtol, atol,
+                                       _stream(stream), C.byref(t), C.byref(b), C.byref(ms)))
+        return {"team": t.value, "block": b.value, "sample_ms": ms.value}
+
     def kernel_config(self, opts: Optional[IntOpts] = None):
         o = opts or self.opts()
         t, b, s, r = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         _check(self._lib.chem_kernel_config(self._h, C.byref(o), C.byref(t), C.byref(b),
                                             C.byref(s), C.byref(r)))
         return {"team": t.value, "block": b.value, "smem": s.value, "regs": r.value}
+
+
+class Tape:
+    """Device memory of one checkpointed forward (chem_tape)."""
+
+    def __init__(self, buf, n_cells, capacity, interval):
+        self.buf = buf
+        self.n_cells, self.capacity, self.interval = n_cells, capacity, interval
+        self.struct = TapeStruct(buf.data_ptr(), buf.numel(), n_cells, capacity, interval)
+
+    def n_accepted(self):
+        """Accepted steps per cell (int32 [n_cells] view of the tape's first block)."""
+        import torch
+        return self.buf[: 4 * self.n_cells].view(torch.int32)
+
+
+def chem_integrate_fn():
+    """torch.autograd.Function: (T0 [C], Y0 [Ns, C], lnA [Nr]) -> (T [C], Y [Ns, C]) with
+    gradients from the checkpointed discrete adjoint."""
+    import torch
+
+    class ChemIntegrate(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, T0, Y0, lnA, mech, P, dt, rtol, atol, capacity, interval):
+            T, Y = T0.detach().clone(), Y0.detach().clone()
+            lnA = lnA.detach().contiguous()
+            tape = mech.make_tape(T.shape[0], capacity, interval, device=T.device)
+            status = torch.empty(T.shape[0], dtype=torch.int32, device=T.device)
+            mech.integrate_ckpt(T, P, Y, dt, tape, rtol=rtol, atol=atol, status=status,
+                                opts=mech.opts(lnA=lnA))
+            ctx.mech, ctx.tape, ctx.lnA = mech, tape, lnA
+            ctx.save_for_backward(P)
+            ctx.status = status
+            return T, Y
+
+        @staticmethod
+        def backward(ctx, gT, gY):
+            (P,) = ctx.saved_tensors
+            T_like = P
+            gT = torch.zeros_like(T_like) if gT is None else gT.contiguous()
+            gY = (torch.zeros((ctx.mech.ns, P.shape[0]), dtype=torch.float64, device=P.device)
+                  if gY is None else gY.contiguous())
+            g_lnA, gT0, gY0 = ctx.mech.adjoint(P, gT, gY, ctx.tape,
+                                               opts=ctx.mech.opts(lnA=ctx.lnA))
+            return gT0, gY0, g_lnA, None, None, None, None, None, None, None
+
+    return ChemIntegrate

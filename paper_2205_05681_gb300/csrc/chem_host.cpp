@@ -61,7 +61,9 @@ namespace drv {
   X(cuModuleUnload) X(cuModuleGetFunction) X(cuModuleGetGlobal) X(cuFuncSetAttribute)           \
   X(cuFuncGetAttribute) X(cuOccupancyMaxActiveBlocksPerMultiprocessor) X(cuLaunchKernel)         \
   X(cuMemsetD32Async) X(cuMemcpyDtoH) X(cuMemcpyDtoHAsync) X(cuMemcpyHtoDAsync)                 \
-  X(cuStreamSynchronize) X(cuMemHostAlloc) X(cuMemFreeHost) X(cuMemAlloc) X(cuMemFree)
+  X(cuStreamSynchronize) X(cuMemHostAlloc) X(cuMemFreeHost) X(cuMemAlloc) X(cuMemFree)            \
+  X(cuEventCreate) X(cuEventRecord) X(cuEventSynchronize) X(cuEventElapsedTime) X(cuEventDestroy) \
+  X(cuMemcpyDtoDAsync)
 #define CHEM_DECL(fn) decltype(&::fn) fn = nullptr;
 CHEM_DRV_FUNCS(CHEM_DECL)
 #undef CHEM_DECL
@@ -88,6 +90,7 @@ bool load() {
 // ------------------------------------------------------------------------------ mechanism data
 
 constexpr int kMaxSide = 3;  // distinct species per reaction side
+constexpr size_t kSegLen = 8;  // entries per omega-gather segment
 
 struct SpeciesData {
   std::string name;
@@ -280,10 +283,11 @@ void emit_array(std::ostringstream& o, const char* type, const char* name, const
   o << "};\n";
 }
 
-std::string emit_mechanism(const MechData& m, int team, int tpb) {
+std::string emit_mechanism(const MechData& m, int team, int tpb, bool adjoint) {
   const int ns = (int)m.sp.size(), nr = (int)m.rx.size();
   std::ostringstream o;
   o << "// generated for mechanism " << m.name << "\n";
+  if (adjoint) o << "#define CHEM_ADJOINT 1\n";
   o << "#define NS " << ns << "\n#define NR " << nr << "\n#define TEAM " << team << "\n#define TPB " << tpb
     << "\n#define MAXP " << kMaxSide << "\n";
   Ros4Coefficients c;
@@ -375,6 +379,32 @@ std::string emit_mechanism(const MechData& m, int team, int tpb) {
       << num(tr ? 1.0 / t[2] : 0.0) << "," << num(tr ? t[3] : 0.0) << "}";
   }
   o << "};\n";
+  // species -> (reaction, net nu) lists cut into segments of at most kSegLen entries for the
+  // deterministic omega gather of multi-lane teams
+  std::vector<int> gbeg(1, 0), grx, spseg(1, 0);
+  std::vector<double> gnu;
+  for (int k = 0; k < ns; ++k) {
+    std::vector<std::pair<int, int>> lst;
+    for (int r = 0; r < nr; ++r) {
+      int nu = 0;
+      for (int i = 0; i < m.rx[r].npr; ++i) if (m.rx[r].psp[i] == k) nu += m.rx[r].pnu[i];
+      for (int i = 0; i < m.rx[r].nre; ++i) if (m.rx[r].rsp[i] == k) nu -= m.rx[r].rnu[i];
+      if (nu) lst.push_back({r, nu});
+    }
+    for (size_t a = 0; a < lst.size(); a += kSegLen) {
+      for (size_t b = a; b < std::min(lst.size(), a + kSegLen); ++b) { grx.push_back(lst[b].first); gnu.push_back(lst[b].second); }
+      gbeg.push_back((int)grx.size());
+    }
+    spseg.push_back((int)gbeg.size() - 1);
+  }
+  const int nseg = (int)gbeg.size() - 1, nent = std::max<int>(1, (int)grx.size());
+  o << "#define NSEG " << std::max(nseg, 1) << "\n";
+  emit_array(o, "int", "mk_gseg_beg", "[" + std::to_string(nseg + 1) + "]", nseg + 1, [&](int i) { return std::to_string(gbeg[i]); });
+  emit_array(o, "int", "mk_gent_rx", "[" + std::to_string(nent) + "]", nent,
+             [&](int i) { return std::to_string(i < (int)grx.size() ? grx[i] : 0); });
+  emit_array(o, "double", "mk_gent_nu", "[" + std::to_string(nent) + "]", nent,
+             [&](int i) { return num(i < (int)gnu.size() ? gnu[i] : 0.0); });
+  emit_array(o, "int", "mk_spseg_beg", "[" + std::to_string(ns + 1) + "]", ns + 1, [&](int i) { return std::to_string(spseg[i]); });
   o << kDeviceSource;
   o << "\nextern \"C\" __device__ const int chem_slots = SLOTS;\n";
   return o.str();
@@ -416,9 +446,9 @@ int nvrtc_compile(const std::string& src, const std::string& name, std::string* 
 }
 
 // cubin for (mechanism, team, block): from cache_dir if present, else compiled (and stored)
-int build_cubin(const MechData& m, int team, int tpb, const char* cache_dir, bool verbose, std::string* cubin,
-                std::string* log) {
-  const std::string src = emit_mechanism(m, team, tpb);
+int build_cubin(const MechData& m, int team, int tpb, bool adjoint, const char* cache_dir, bool verbose,
+                std::string* cubin, std::string* log) {
+  const std::string src = emit_mechanism(m, team, tpb, adjoint);
   int major = 0, minor = 0;
   nvrtcVersion(&major, &minor);
   std::string key = src;
@@ -428,8 +458,8 @@ int build_cubin(const MechData& m, int team, int tpb, const char* cache_dir, boo
   snprintf(hex, sizeof(hex), "%016llx", (unsigned long long)fnv1a(key));
   std::string path;
   if (cache_dir && *cache_dir) {
-    path = std::string(cache_dir) + "/" + m.name + "_t" + std::to_string(team) + "_b" + std::to_string(tpb) + "_" +
-           hex + ".cubin";
+    path = std::string(cache_dir) + "/" + m.name + (adjoint ? "_adj" : "") + "_t" + std::to_string(team) + "_b" +
+           std::to_string(tpb) + "_" + hex + ".cubin";
     std::ifstream in(path, std::ios::binary);
     if (in) {
       std::ostringstream ss;
@@ -459,8 +489,10 @@ struct Module {
   int team = 0, tpb = 0;
   CUmodule mod = nullptr;
   CUfunction f_source = nullptr, f_jac = nullptr, f_int = nullptr, f_pinit = nullptr, f_patt = nullptr,
-             f_pfin = nullptr;
+             f_pfin = nullptr, f_adj = nullptr, f_adjred = nullptr, f_vjp = nullptr;
   int smem = 0;          // dynamic shared memory per block
+  int adj_smem = 0;      // ... of the adjoint / VJP kernels (0: not available for this config)
+  int adj_occ = 0;
   int occ = 0;           // resident blocks per SM for f_int
   int regs = 0;
 };
@@ -476,7 +508,8 @@ struct chem_mech {
   int default_team = 32, default_tpb = 64;
   std::mutex mu;       // guards modules
   std::mutex host_mu;  // guards the chem_integrate_host buffers
-  std::map<std::pair<int, int>, std::unique_ptr<Module>> modules;
+  std::map<std::pair<int, int>, std::unique_ptr<Module>> modules;      // forward kernels
+  std::map<std::pair<int, int>, std::unique_ptr<Module>> adj_modules;  // + adjoint kernels
   // plain-mode host mirror of the activity counter and host-API buffers
   unsigned int* pinned = nullptr;
   CUdeviceptr host_api_buf = 0;
@@ -485,7 +518,27 @@ struct chem_mech {
 
 namespace {
 
-int slots_for(int ns) { return ns * ns + 22 * ns + 16; }
+int n_segments(const MechData& m) {
+  const int ns = (int)m.sp.size();
+  int nseg = 0;
+  for (int k = 0; k < ns; ++k) {
+    size_t cnt = 0;
+    for (auto& x : m.rx) {
+      int nu = 0;
+      for (int i = 0; i < x.npr; ++i) if (x.psp[i] == k) nu += x.pnu[i];
+      for (int i = 0; i < x.nre; ++i) if (x.rsp[i] == k) nu -= x.rnu[i];
+      if (nu) ++cnt;
+    }
+    nseg += (int)((cnt + kSegLen - 1) / kSegLen);
+  }
+  return std::max(nseg, 1);
+}
+
+// shared-memory slots of one cell; mirrors the OFF_* layout of ros4_device.cuh
+int slots_for(const MechData& m) {
+  const int ns = (int)m.sp.size(), nr = (int)m.rx.size();
+  return ns * ns + 23 * ns + nr + n_segments(m) + 16;
+}
 
 void default_config(int ns, int* team, int* tpb) {
   if (ns <= 24) { *team = 32; *tpb = 128; }
@@ -500,19 +553,19 @@ int check_config(int team, int tpb) {
   return fail(CHEM_EARG, "unsupported kernel config team=%d block=%d", team, tpb);
 }
 
-int smem_bytes(int ns, int team, int tpb) {
+int smem_bytes(const MechData& m, int team, int tpb) {
   const int teams = team == 1 ? tpb : (team == 32 ? tpb / 32 : 1);
-  return slots_for(ns) * 8 * teams;
+  return slots_for(m) * 8 * teams;
 }
 
-int get_module(chem_mech* m, int team, int tpb, Module** out) {
+int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = false) {
   std::lock_guard<std::mutex> lk(m->mu);
   auto key = std::make_pair(team, tpb);
-  auto it = m->modules.find(key);
-  if (it != m->modules.end()) { *out = it->second.get(); return 0; }
+  auto& mods = adjoint ? m->adj_modules : m->modules;
+  auto it = mods.find(key);
+  if (it != mods.end()) { *out = it->second.get(); return 0; }
   if (int rc = check_config(team, tpb)) return rc;
-  const int ns = (int)m->data.sp.size();
-  const int smem = smem_bytes(ns, team, tpb);
+  const int smem = smem_bytes(m->data, team, tpb);
   int max_optin = 0;
   CUdevice dev;
   CU_TRY(drv::cuCtxGetDevice(&dev));
@@ -520,7 +573,7 @@ int get_module(chem_mech* m, int team, int tpb, Module** out) {
   if (smem > max_optin)
     return fail(CHEM_EARG, "config team=%d block=%d needs %d B shared memory (max %d)", team, tpb, smem, max_optin);
   std::string cubin, log;
-  if (int rc = build_cubin(m->data, team, tpb, m->cache_dir.c_str(), m->verbose, &cubin, &log)) return rc;
+  if (int rc = build_cubin(m->data, team, tpb, adjoint, m->cache_dir.c_str(), m->verbose, &cubin, &log)) return rc;
   auto mod = std::make_unique<Module>();
   mod->team = team;
   mod->tpb = tpb;
@@ -537,14 +590,32 @@ int get_module(chem_mech* m, int team, int tpb, Module** out) {
   CU_TRY(drv::cuModuleGetGlobal(&slots_ptr, &slots_sz, mod->mod, "chem_slots"));
   int dev_slots = 0;
   CU_TRY(drv::cuMemcpyDtoH(&dev_slots, slots_ptr, sizeof(int)));
-  if (dev_slots != slots_for(ns)) return fail(CHEM_ECUDA, "shared-memory layout mismatch (%d vs %d)", dev_slots, slots_for(ns));
+  if (dev_slots != slots_for(m->data))
+    return fail(CHEM_ECUDA, "shared-memory layout mismatch (%d vs %d)", dev_slots, slots_for(m->data));
   for (CUfunction f : {mod->f_source, mod->f_jac, mod->f_int, mod->f_pinit, mod->f_patt})
     CU_TRY(drv::cuFuncSetAttribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem));
   CU_TRY(drv::cuOccupancyMaxActiveBlocksPerMultiprocessor(&mod->occ, mod->f_int, tpb, smem));
+  if (adjoint && team > 1) {
+    CUdeviceptr ap;
+    size_t asz;
+    CU_TRY(drv::cuModuleGetGlobal(&ap, &asz, mod->mod, "chem_aslots"));
+    int aslots = 0;
+    CU_TRY(drv::cuMemcpyDtoH(&aslots, ap, sizeof(int)));
+    const int asmem = aslots * 8 * (team == 32 ? tpb / 32 : 1);
+    if (asmem <= max_optin) {
+      CU_TRY(drv::cuModuleGetFunction(&mod->f_adj, mod->mod, "chem_adjoint_k"));
+      CU_TRY(drv::cuModuleGetFunction(&mod->f_adjred, mod->mod, "chem_adjoint_reduce_k"));
+      CU_TRY(drv::cuModuleGetFunction(&mod->f_vjp, mod->mod, "chem_eval_vjp_k"));
+      CU_TRY(drv::cuFuncSetAttribute(mod->f_adj, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, asmem));
+      CU_TRY(drv::cuFuncSetAttribute(mod->f_vjp, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, asmem));
+      CU_TRY(drv::cuOccupancyMaxActiveBlocksPerMultiprocessor(&mod->adj_occ, mod->f_adj, tpb, asmem));
+      if (mod->adj_occ >= 1) mod->adj_smem = asmem;
+    }
+  }
   CU_TRY(drv::cuFuncGetAttribute(&mod->regs, CU_FUNC_ATTRIBUTE_NUM_REGS, mod->f_int));
   if (mod->occ < 1) return fail(CHEM_ECUDA, "config team=%d block=%d cannot be resident", team, tpb);
   *out = mod.get();
-  m->modules[key] = std::move(mod);
+  mods[key] = std::move(mod);
   return 0;
 }
 
@@ -619,7 +690,9 @@ int chem_mech_compile_only(const char* spec_path, const chem_build_opts* opts, c
   if (opts && opts->team > 0) { team = opts->team; tpb = opts->block > 0 ? opts->block : tpb; }
   if (int rc = check_config(team, tpb)) return rc;
   std::string cubin, lg;
-  int rc = build_cubin(d, team, tpb, opts ? opts->cache_dir : nullptr, opts && opts->verbose, &cubin, &lg);
+  const bool adj = opts && opts->adjoint;
+  if (adj && team == 1) return fail(CHEM_EARG, "the adjoint needs a multi-lane configuration (team >= 32)");
+  int rc = build_cubin(d, team, tpb, adj, opts ? opts->cache_dir : nullptr, opts && opts->verbose, &cubin, &lg);
   if (log && log_cap) {
     const size_t n = std::min(lg.size(), log_cap - 1);
     memcpy(log, lg.data(), n);
@@ -665,6 +738,7 @@ int chem_mech_free(chem_mech_t m) {
   if (!m) return 0;
   drv::cuCtxSetCurrent(m->ctx);
   for (auto& kv : m->modules) drv::cuModuleUnload(kv.second->mod);
+  for (auto& kv : m->adj_modules) drv::cuModuleUnload(kv.second->mod);
   if (m->pinned) drv::cuMemFreeHost(m->pinned);
   if (m->host_api_buf) drv::cuMemFree(m->host_api_buf);
   delete m;
@@ -758,8 +832,12 @@ int chem_integrate(chem_mech_t m, int64_t n_cells, double* T, const double* P, d
   if (mode == CHEM_MODE_PERSISTENT) {
     CUdeviceptr q = (CUdeviceptr)ws;
     CU_TRY(drv::cuMemsetD32Async(q, 0, 2, s));
+    int* tnacc = nullptr;
+    double* th = nullptr;
+    double* tck = nullptr;
+    int cap = 0, interval = 1;
     void* args[] = {&nc, &T, (void*)&P, &Y, &l, &dt, &rtol, &atol, &h, &status, &att, (void*)&lnA,
-                    &max_steps, &h_min, &T_min, &q};
+                    &max_steps, &h_min, &T_min, &q, &tnacc, &th, &tck, &cap, &interval};
     return launch(mod->f_int, grid_for(m, mod, n_cells), mod, stream, args);
   }
   if (mode != CHEM_MODE_PLAIN) return fail(CHEM_EARG, "unknown mode %d", mode);
@@ -838,6 +916,215 @@ int chem_integrate_host(chem_mech_t m, int64_t n_cells, double* T, const double*
   if (h) CU_TRY(drv::cuMemcpyDtoHAsync(h, b + offH, 8 * n, s));
   if (status) CU_TRY(drv::cuMemcpyDtoHAsync(status, b + offS, 4 * n, s));
   CU_TRY(drv::cuStreamSynchronize(s));
+  return 0;
+}
+
+// ------------------------------------------------------------------------------ adjoint
+
+static size_t tape_ck_count(int cap, int interval) { return (size_t)((cap - 1) / interval + 1); }
+
+struct TapeLayout {
+  size_t nacc, h, ck, total;
+};
+
+static TapeLayout tape_layout(int ns, int64_t n, int cap, int interval) {
+  TapeLayout L;
+  size_t o = 0;
+  L.nacc = o; o = align256(o + sizeof(int) * n);
+  L.h = o; o = align256(o + sizeof(double) * n * (size_t)cap);
+  L.ck = o; o = align256(o + sizeof(double) * n * ns * tape_ck_count(cap, interval));
+  L.total = o;
+  return L;
+}
+
+size_t chem_tape_bytes(chem_mech_t m, int64_t n_cells, int32_t capacity, int32_t interval) {
+  if (!m || n_cells < 0 || capacity < 1 || interval < 1) return 0;
+  return tape_layout((int)m->data.sp.size(), n_cells, capacity, interval).total;
+}
+
+static int check_tape(chem_mech_t m, int64_t n_cells, const chem_tape* t) {
+  if (!t || !t->mem) return fail(CHEM_EARG, "NULL tape");
+  if (t->n_cells != n_cells) return fail(CHEM_EARG, "tape was sized for %lld cells", (long long)t->n_cells);
+  if (t->capacity < 1 || t->interval < 1) return fail(CHEM_EARG, "tape capacity and interval must be >= 1");
+  if (t->bytes < chem_tape_bytes(m, n_cells, t->capacity, t->interval)) return fail(CHEM_EWS, "tape memory too small");
+  if (((uintptr_t)t->mem) & 255) return fail(CHEM_EARG, "tape memory must be 256-byte aligned");
+  return 0;
+}
+
+int chem_integrate_ckpt(chem_mech_t m, int64_t n_cells, double* T, const double* P, double* Y, int64_t ld, double dt,
+                        double rtol, double atol, double* h, int32_t* status, const chem_int_opts* o,
+                        const chem_tape* tape, void* ws, size_t ws_bytes, void* stream) {
+  if (!m) return fail(CHEM_EARG, "NULL mechanism");
+  if (int rc = check_cells(n_cells, ld)) return rc;
+  if (!(dt > 0) || !(rtol > 0) || !(atol > 0) || !std::isfinite(dt))
+    return fail(CHEM_EARG, "dt, rtol and atol must be positive and finite");
+  if (n_cells == 0) return 0;
+  if (!T || !P || !Y) return fail(CHEM_EARG, "NULL array");
+  if (int rc = check_tape(m, n_cells, tape)) return rc;
+  if (o && o->mode != CHEM_MODE_PERSISTENT) return fail(CHEM_EARG, "the checkpointed forward is persistent only");
+  if (!ws || ws_bytes < 256 || (((uintptr_t)ws) & 255)) return fail(CHEM_EWS, "workspace of 256 aligned bytes needed");
+  int max_steps = (o && o->max_steps > 0) ? o->max_steps : 100000;
+  double h_min = (o && o->h_min > 0) ? o->h_min : 1e-20;
+  double T_min = o ? o->T_min : 0.0;
+  const double* lnA = o ? o->lnA : nullptr;
+  int* att = o ? o->attempts : nullptr;
+  if (int rc = make_current(m)) return rc;
+  Module* mod;
+  if (int rc = resolve(m, o, &mod)) return rc;
+  const TapeLayout L = tape_layout((int)m->data.sp.size(), n_cells, tape->capacity, tape->interval);
+  char* b = (char*)tape->mem;
+  int* tnacc = (int*)(b + L.nacc);
+  double* th = (double*)(b + L.h);
+  double* tck = (double*)(b + L.ck);
+  int cap = tape->capacity, interval = tape->interval;
+  long long nc = n_cells, l = ld;
+  CUdeviceptr q = (CUdeviceptr)ws;
+  CU_TRY(drv::cuMemsetD32Async(q, 0, 2, (CUstream)stream));
+  void* args[] = {&nc, &T, (void*)&P, &Y, &l, &dt, &rtol, &atol, &h, &status, &att, (void*)&lnA,
+                  &max_steps, &h_min, &T_min, &q, &tnacc, &th, &tck, &cap, &interval};
+  return launch(mod->f_int, grid_for(m, mod, n_cells), mod, stream, args);
+}
+
+static int adjoint_module(chem_mech_t m, const chem_int_opts* o, Module** mod) {
+  Module* fwd;
+  if (int rc = resolve(m, o, &fwd)) return rc;
+  if (fwd->team == 1) return fail(CHEM_EARG, "the adjoint needs a multi-lane configuration (team >= 32)");
+  if (int rc = get_module(m, fwd->team, fwd->tpb, mod, true)) return rc;
+  if (!(*mod)->f_adj)
+    return fail(CHEM_EARG, "the adjoint needs a multi-lane configuration (team >= 32) that fits shared memory");
+  return 0;
+}
+
+static int64_t adjoint_teams(const chem_mech* m, const Module* mod, int64_t n_cells) {
+  const int64_t tpb = teams_per_block(mod);
+  const int64_t need = (n_cells + tpb - 1) / tpb;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)m->n_sm * mod->adj_occ));
+  return grid * tpb;
+}
+
+size_t chem_adjoint_workspace(chem_mech_t m, int64_t n_cells, const chem_int_opts* o, int32_t interval) {
+  if (!m || n_cells < 0 || interval < 1) return 0;
+  if (make_current(m)) return 0;
+  Module* mod;
+  if (adjoint_module(m, o, &mod)) return 0;
+  const int ns = (int)m->data.sp.size(), nr = (int)m->data.rx.size();
+  const int64_t teams = adjoint_teams(m, mod, std::max<int64_t>(n_cells, 1));
+  return 256 + align256(sizeof(double) * teams * (size_t)interval * ns) + align256(sizeof(double) * teams * nr);
+}
+
+int chem_adjoint(chem_mech_t m, int64_t n_cells, const double* P, const double* gT, const double* gY, int64_t ld,
+                 const chem_tape* tape, const chem_int_opts* o, double* g_lnA, double* gT0, double* gY0, void* ws,
+                 size_t ws_bytes, void* stream) {
+  if (!m) return fail(CHEM_EARG, "NULL mechanism");
+  if (int rc = check_cells(n_cells, ld)) return rc;
+  if (!P || !gT || !gY || !g_lnA || !gT0 || !gY0) return fail(CHEM_EARG, "NULL array");
+  if (int rc = check_tape(m, n_cells, tape)) return rc;
+  if (int rc = make_current(m)) return rc;
+  Module* mod;
+  if (int rc = adjoint_module(m, o, &mod)) return rc;
+  const size_t need = chem_adjoint_workspace(m, n_cells, o, tape->interval);
+  if (!ws || ws_bytes < need) return fail(CHEM_EWS, "adjoint workspace of %zu bytes needed, %zu given", need, ws_bytes);
+  if (((uintptr_t)ws) & 255) return fail(CHEM_EARG, "workspace must be 256-byte aligned");
+  const int ns = (int)m->data.sp.size(), nr = (int)m->data.rx.size();
+  CUstream s = (CUstream)stream;
+  if (n_cells == 0) {
+    CU_TRY(drv::cuMemsetD32Async((CUdeviceptr)g_lnA, 0, 2 * (size_t)nr, s));
+    return 0;
+  }
+  const int64_t teams = adjoint_teams(m, mod, n_cells);
+  char* b = (char*)ws;
+  CUdeviceptr q = (CUdeviceptr)b;
+  double* seg = (double*)(b + 256);
+  double* part = (double*)(b + 256 + align256(sizeof(double) * teams * (size_t)tape->interval * ns));
+  const TapeLayout L = tape_layout(ns, n_cells, tape->capacity, tape->interval);
+  char* tb = (char*)tape->mem;
+  const int* tnacc = (const int*)(tb + L.nacc);
+  const double* th = (const double*)(tb + L.h);
+  const double* tck = (const double*)(tb + L.ck);
+  const double* lnA = o ? o->lnA : nullptr;
+  int interval = tape->interval;
+  long long nc = n_cells, l = ld, nparts = teams;
+  CU_TRY(drv::cuMemsetD32Async(q, 0, 2, s));
+  void* args[] = {&nc, (void*)&P, (void*)&gT, (void*)&gY, &l, &gT0, &gY0, (void*)&lnA, (void*)&tnacc, (void*)&th,
+                  (void*)&tck, &interval, &seg, &part, &q};
+  const unsigned grid = (unsigned)(teams / teams_per_block(mod));
+  CU_TRY(drv::cuLaunchKernel(mod->f_adj, grid, 1, 1, mod->tpb, 1, 1, mod->adj_smem, s, args, nullptr));
+  void* rargs[] = {&nparts, &part, &g_lnA};
+  CU_TRY(drv::cuLaunchKernel(mod->f_adjred, (unsigned)((nr + 127) / 128), 1, 1, 128, 1, 1, 0, s, rargs, nullptr));
+  return 0;
+}
+
+int chem_eval_vjp(chem_mech_t m, int64_t n_cells, const double* T, const double* P, const double* n, const double* v,
+                  double* gy, double* gp, int64_t ld, const double* lnA, void* stream) {
+  if (!m) return fail(CHEM_EARG, "NULL mechanism");
+  if (int rc = check_cells(n_cells, ld)) return rc;
+  if (n_cells == 0) return 0;
+  if (!T || !P || !n || !v || !gy || !gp) return fail(CHEM_EARG, "NULL array");
+  if (int rc = make_current(m)) return rc;
+  Module* mod;
+  if (int rc = adjoint_module(m, nullptr, &mod)) return rc;
+  long long nc = n_cells, l = ld;
+  void* args[] = {&nc, (void*)&T, (void*)&P, (void*)&n, (void*)&v, &gy, &gp, &l, (void*)&lnA};
+  const int64_t tpb = teams_per_block(mod);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_cells + tpb - 1) / tpb, (int64_t)m->n_sm * mod->adj_occ));
+  CU_TRY(drv::cuLaunchKernel(mod->f_vjp, grid, 1, 1, mod->tpb, 1, 1, mod->adj_smem, (CUstream)stream, args, nullptr));
+  return 0;
+}
+
+int chem_autotune(chem_mech_t m, int64_t n_cells, const double* T, const double* P, const double* Y, int64_t ld,
+                  double dt, double rtol, double atol, void* stream, int32_t* team_out, int32_t* block_out,
+                  float* ms_out) {
+  if (!m) return fail(CHEM_EARG, "NULL mechanism");
+  if (int rc = check_cells(n_cells, ld)) return rc;
+  if (n_cells == 0 || !T || !P || !Y) return fail(CHEM_EARG, "autotune needs a non-empty sample");
+  if (int rc = make_current(m)) return rc;
+  const int ns = (int)m->data.sp.size();
+  const int64_t n = std::min<int64_t>(n_cells, 4096);
+  CUstream s = (CUstream)stream;
+  // private copy of the sample: T, P, Y [ns][n], h, workspace
+  const size_t oT = 0, oP = align256(8 * n), oY = align256(oP + 8 * n), oY0 = align256(oY + 8 * n * ns),
+               oT0 = align256(oY0 + 8 * n * ns), oW = align256(oT0 + 8 * n), total = oW + 256;
+  CUdeviceptr buf = 0;
+  CU_TRY(drv::cuMemAlloc(&buf, total));
+  struct Free { CUdeviceptr p; ~Free() { if (p) drv::cuMemFree(p); } } guard{buf};
+  CU_TRY(drv::cuMemcpyDtoDAsync(buf + oT0, (CUdeviceptr)T, 8 * n, s));
+  CU_TRY(drv::cuMemcpyDtoDAsync(buf + oP, (CUdeviceptr)P, 8 * n, s));
+  for (int k = 0; k < ns; ++k)
+    CU_TRY(drv::cuMemcpyDtoDAsync(buf + oY0 + 8 * n * k, (CUdeviceptr)(Y + (size_t)k * ld), 8 * n, s));
+  std::vector<std::pair<int, int>> cand = {{32, 32}, {32, 64}, {64, 64}, {128, 128}, {256, 256}};
+  if (ns <= 16) cand.insert(cand.begin(), {1, 32});
+  CUevent e0, e1;
+  CU_TRY(drv::cuEventCreate(&e0, 0));
+  CU_TRY(drv::cuEventCreate(&e1, 0));
+  float best = 1e30f;
+  int bt = m->default_team, bb = m->default_tpb;
+  for (auto& c : cand) {
+    Module* mod = nullptr;
+    if (get_module(m, c.first, c.second, &mod) != 0) continue;  // does not fit: skip
+    chem_int_opts o{};
+    o.team = c.first;
+    o.block = c.second;
+    float ms = 0;
+    for (int rep = 0; rep < 2; ++rep) {
+      CU_TRY(drv::cuMemcpyDtoDAsync(buf + oT, buf + oT0, 8 * n, s));
+      CU_TRY(drv::cuMemcpyDtoDAsync(buf + oY, buf + oY0, 8 * n * ns, s));
+      CU_TRY(drv::cuEventRecord(e0, s));
+      int rc = chem_integrate(m, n, (double*)(buf + oT), (const double*)(buf + oP), (double*)(buf + oY), n, dt, rtol,
+                              atol, nullptr, nullptr, &o, (void*)(buf + oW), 256, stream);
+      if (rc) return rc;
+      CU_TRY(drv::cuEventRecord(e1, s));
+      CU_TRY(drv::cuEventSynchronize(e1));
+      CU_TRY(drv::cuEventElapsedTime(&ms, e0, e1));
+    }
+    if (ms < best) { best = ms; bt = c.first; bb = c.second; }
+  }
+  drv::cuEventDestroy(e0);
+  drv::cuEventDestroy(e1);
+  m->default_team = bt;
+  m->default_tpb = bb;
+  if (team_out) *team_out = bt;
+  if (block_out) *block_out = bb;
+  if (ms_out) *ms_out = best;
   return 0;
 }
 

@@ -44,6 +44,7 @@
 #define ST_H_UNDERFLOW 2
 #define ST_NONFINITE 3
 #define ST_SKIPPED 4
+#define ST_TAPE_FULL 5
 
 #define NEQ NS
 #define BATH (NS - 1)
@@ -80,7 +81,10 @@
 #define OFF_BE (OFF_AL + NS)
 #define OFF_JT (OFF_BE + NS)
 #define OFF_PIV (OFF_JT + NS)
-#define OFF_RED (OFF_PIV + NEQ)
+#define OFF_PERM (OFF_PIV + NEQ)
+#define OFF_Q (OFF_PERM + NEQ)
+#define OFF_SEG (OFF_Q + NR)
+#define OFF_RED (OFF_SEG + NSEG)
 #define SLOTS (OFF_RED + 16)
 
 // ------------------------------------------------------------------------------ team plumbing
@@ -99,6 +103,7 @@ struct Team {
   __device__ __forceinline__ double& at(int o, int i) const { return base[(o + i) * SS]; }
   __device__ __forceinline__ double& A(int i, int j) const { return base[(OFF_A + i * NEQ + j) * SS]; }
   __device__ __forceinline__ int& piv(int i) const { return *reinterpret_cast<int*>(&base[(OFF_PIV + i) * SS]); }
+  __device__ __forceinline__ int& perm(int i) const { return *reinterpret_cast<int*>(&base[(OFF_PERM + i) * SS]); }
 };
 
 // sum over the team; every lane gets the same bits (butterfly with commutative adds)
@@ -296,8 +301,12 @@ __device__ __forceinline__ void reaction_loop(const Team& tm, const CellScalars&
     const double m = kind == THIRD ? M : 1.0;
     const double qnet = fwd - rev;
     const double q = m * qnet;
-    for (int i = 0; i < nre; ++i) scatter_add<double>(&tm.at(OFF_OM, mk_rsp[r][i]), -mk_rnu[r][i] * q);
-    for (int i = 0; i < npr; ++i) scatter_add<double>(&tm.at(OFF_OM, mk_psp[r][i]), mk_pnu[r][i] * q);
+#if TEAM == 1
+    for (int i = 0; i < nre; ++i) tm.at(OFF_OM, mk_rsp[r][i]) -= mk_rnu[r][i] * q;
+    for (int i = 0; i < npr; ++i) tm.at(OFF_OM, mk_psp[r][i]) += mk_pnu[r][i] * q;
+#else
+    tm.at(OFF_Q, r) = q;  // omega is gathered per species below (no atomics, fixed order)
+#endif
     if (WJ) {
       // d ln Kc / dT = (sum nu'' h/RT - sum nu' h/RT - dnu) / T
       double dlKc = -dnu;
@@ -351,6 +360,22 @@ __device__ __forceinline__ void reaction_loop(const Team& tm, const CellScalars&
     }
   }
   tsync();
+#if TEAM > 1
+  // omega_k = sum_r nu_kr q_r: fixed-length segments of each species' reaction list are summed
+  // by separate lanes, then each species adds its segments in order (deterministic)
+  for (int sg = tm.tl; sg < NSEG; sg += TEAM) {
+    double acc = 0.0;
+    for (int e = mk_gseg_beg[sg]; e < mk_gseg_beg[sg + 1]; ++e) acc += mk_gent_nu[e] * tm.at(OFF_Q, mk_gent_rx[e]);
+    tm.at(OFF_SEG, sg) = acc;
+  }
+  tsync();
+  for (int k = tm.tl; k < NS; k += TEAM) {
+    double acc = 0.0;
+    for (int sg = mk_spseg_beg[k]; sg < mk_spseg_beg[k + 1]; ++sg) acc += tm.at(OFF_SEG, sg);
+    tm.at(OFF_OM, k) = acc;
+  }
+  tsync();
+#endif
 }
 
 // f from omega: f[0] = dT/dt = -T sum_k (h_k/RT) V omega_k / sum_k n_k cp_k/R,
@@ -474,9 +499,8 @@ __device__ void eval_f_jac(const Team& tm, int oy, int of, double P, const doubl
 // ------------------------------------------------------------------------------ LU + solves
 
 // In-place LU with partial pivoting of A (N x N): largest |a| in the column, lowest row on
-// ties.  Pivots in OFF_PIV (row swapped with k at step k), 1/U_kk in OFF_INVD, and the
-// composed permutation in OFF_TMP (as ints in the PIV slots' neighbours is avoided: TMP holds
-// perm as doubles of exact small integers).
+// ties.  Row swapped with k at step k in OFF_PIV, 1/U_kk in OFF_INVD, and the composed row
+// permutation (row i of P A is row perm[i] of A) in OFF_PERM for the solves.
 __device__ void lu_factor(const Team& tm) {
 #if TEAM == 1
   for (int k = 0; k < NEQ; ++k) {
@@ -532,61 +556,137 @@ __device__ void lu_factor(const Team& tm) {
     if (tm.tl == 0) { tm.piv(k) = p; tm.at(OFF_INVD, k) = inv; }
     for (int i = k + 1 + tm.tl; i < NEQ; i += TEAM) tm.A(i, k) *= inv;
     tsync();
+    // trailing update A[i][j] -= L[i][k] U[k][j], i, j > k, flattened over the m x m block;
+    // four independent elements per iteration so that loads and DFMAs overlap
     const int m = NEQ - k - 1;
     if (m > 0) {
       const int tot = m * m;
       const int qd = TEAM / m, rm = TEAM - qd * m;
-      int i = tm.tl / m, j = tm.tl - (tm.tl / m) * m;
-      for (int e = tm.tl; e < tot; e += TEAM) {
-        tm.A(k + 1 + i, k + 1 + j) -= tm.A(k + 1 + i, k) * tm.A(k, k + 1 + j);
-        i += qd;
-        j += rm;
-        if (j >= m) { j -= m; ++i; }
+      int i0 = tm.tl / m, j0 = tm.tl - i0 * m;
+      for (int e = tm.tl; e < tot; e += 4 * TEAM) {
+        int ii[4], jj[4];
+        ii[0] = i0; jj[0] = j0;
+#pragma unroll
+        for (int t = 1; t < 4; ++t) {
+          ii[t] = ii[t - 1] + qd;
+          jj[t] = jj[t - 1] + rm;
+          if (jj[t] >= m) { jj[t] -= m; ++ii[t]; }
+        }
+        double a[4], l[4], u[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (e + t * TEAM < tot) {
+            a[t] = tm.A(k + 1 + ii[t], k + 1 + jj[t]);
+            l[t] = tm.A(k + 1 + ii[t], k);
+            u[t] = tm.A(k, k + 1 + jj[t]);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (e + t * TEAM < tot) tm.A(k + 1 + ii[t], k + 1 + jj[t]) = a[t] - l[t] * u[t];
+        i0 = ii[3] + qd;
+        j0 = jj[3] + rm;
+        if (j0 >= m) { j0 -= m; ++i0; }
       }
     }
     tsync();
   }
 #endif
+  // composed permutation for the solves
+  if (tm.tl == 0) {
+    for (int i = 0; i < NEQ; ++i) tm.perm(i) = i;
+    for (int k = 0; k < NEQ; ++k) {
+      const int p = tm.piv(k);
+      if (p != k) { const int t = tm.perm(k); tm.perm(k) = tm.perm(p); tm.perm(p) = t; }
+    }
+  }
+  tsync();
 }
 
-// Solve (LU) x = b in place on the vector at slot ob.  With TEAM > 1 only the first warp works.
+// Solve (LU) x = P b in place on the vector at slot ob (P from the pivoting).  With TEAM > 1
+// the first warp works: forward and back substitution in 4 x 4 diagonal blocks (each lane
+// solves the small block redundantly, then updates its rows with four FMAs per block).
 __device__ void lu_solve(const Team& tm, int ob) {
 #if TEAM == 1
-  for (int k = 0; k < NEQ; ++k) {
-    const int p = tm.piv(k);
-    if (p != k) { const double t = tm.at(ob, k); tm.at(ob, k) = tm.at(ob, p); tm.at(ob, p) = t; }
-  }
+  for (int i = 0; i < NEQ; ++i) tm.at(OFF_TMP, i) = tm.at(ob, tm.perm(i));
   for (int i = 0; i < NEQ; ++i) {
-    double s = tm.at(ob, i);
-    for (int j = 0; j < i; ++j) s -= tm.A(i, j) * tm.at(ob, j);
-    tm.at(ob, i) = s;
+    double s = tm.at(OFF_TMP, i);
+    for (int j = 0; j < i; ++j) s -= tm.A(i, j) * tm.at(OFF_TMP, j);
+    tm.at(OFF_TMP, i) = s;
   }
   for (int i = NEQ - 1; i >= 0; --i) {
-    double s = tm.at(ob, i);
-    for (int j = i + 1; j < NEQ; ++j) s -= tm.A(i, j) * tm.at(ob, j);
+    double s = tm.at(OFF_TMP, i);
+    for (int j = i + 1; j < NEQ; ++j) s -= tm.A(i, j) * tm.at(OFF_TMP, j);
     tm.at(ob, i) = s * tm.at(OFF_INVD, i);
+    tm.at(OFF_TMP, i) = tm.at(ob, i);
   }
 #else
   if (tm.tl < 32) {
     const int ln = tm.tl;
-    if (ln == 0)
-      for (int k = 0; k < NEQ; ++k) {
-        const int p = tm.piv(k);
-        if (p != k) { const double t = tm.at(ob, k); tm.at(ob, k) = tm.at(ob, p); tm.at(ob, p) = t; }
-      }
+    for (int i = ln; i < NEQ; i += 32) tm.at(OFF_TMP, i) = tm.at(ob, tm.perm(i));
     __syncwarp();
-    for (int k = 0; k < NEQ - 1; ++k) {
-      const double xk = tm.at(ob, k);
-      for (int i = k + 1 + ln; i < NEQ; i += 32) tm.at(ob, i) -= tm.A(i, k) * xk;
+    // forward: unit lower triangle
+    for (int k0 = 0; k0 < NEQ; k0 += 4) {
+      const int nb = NEQ - k0 < 4 ? NEQ - k0 : 4;
+      double x[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (t < nb) {
+          double v = tm.at(OFF_TMP, k0 + t);
+#pragma unroll
+          for (int s2 = 0; s2 < t; ++s2) v -= tm.A(k0 + t, k0 + s2) * x[s2];
+          x[t] = v;
+        } else {
+          x[t] = 0.0;
+        }
+      }
+      __syncwarp();
+      for (int i = k0 + nb + ln; i < NEQ; i += 32) {
+        double v = tm.at(OFF_TMP, i);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < nb) v -= tm.A(i, k0 + t) * x[t];
+        tm.at(OFF_TMP, i) = v;
+      }
+      if (ln < nb) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t == ln) tm.at(OFF_TMP, k0 + t) = x[t];
+      }
       __syncwarp();
     }
-    for (int k = NEQ - 1; k >= 0; --k) {
-      const double xk = tm.at(ob, k) * tm.at(OFF_INVD, k);
+    // back: upper triangle with 1/U_kk
+    for (int k1 = NEQ - 1; k1 >= 0; k1 -= 4) {
+      const int nb = k1 + 1 < 4 ? k1 + 1 : 4;  // rows k1, k1-1, .. k1-nb+1
+      double x[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (t < nb) {
+          const int r = k1 - t;
+          double v = tm.at(OFF_TMP, r);
+#pragma unroll
+          for (int s2 = 0; s2 < t; ++s2) v -= tm.A(r, k1 - s2) * x[s2];
+          x[t] = v * tm.at(OFF_INVD, r);
+        } else {
+          x[t] = 0.0;
+        }
+      }
       __syncwarp();
-      if (ln == (k & 31)) tm.at(ob, k) = xk;
-      for (int i = ln; i < k; i += 32) tm.at(ob, i) -= tm.A(i, k) * xk;
+      for (int i = ln; i <= k1 - nb; i += 32) {
+        double v = tm.at(OFF_TMP, i);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < nb) v -= tm.A(i, k1 - t) * x[t];
+        tm.at(OFF_TMP, i) = v;
+      }
+      if (ln < nb) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t == ln) tm.at(OFF_TMP, k1 - t) = x[t];
+      }
       __syncwarp();
     }
+    for (int i = ln; i < NEQ; i += 32) tm.at(ob, i) = tm.at(OFF_TMP, i);
   }
   tsync();
 #endif
@@ -655,6 +755,8 @@ struct Ctl {
   double t, h;
   int attempts, status;
   bool reject_last, done;
+  bool acc;   // the last call accepted a step ...
+  double hh;  // ... of this size
 };
 
 // One attempt plus the controller decision (identical rules to the CPU oracle):
@@ -665,6 +767,7 @@ struct Ctl {
 __device__ __forceinline__ void ros4_advance(const Team& tm, Ctl& c, double P, double dt, double rtol,
                                              double atol, int max_steps, double h_min,
                                              const double* lnA_ext) {
+  c.acc = false;
   if (c.attempts >= max_steps) { c.status = ST_MAX_STEPS; c.done = true; return; }
   if (c.h < h_min) { c.status = ST_H_UNDERFLOW; c.done = true; return; }
   const bool last = c.t + 1.0001 * c.h >= dt;
@@ -683,6 +786,8 @@ __device__ __forceinline__ void ros4_advance(const Team& tm, Ctl& c, double P, d
     tsync();
     if (c.reject_last && fac > 1.0) fac = 1.0;
     c.reject_last = false;
+    c.acc = true;
+    c.hh = hh;
     const double hnext = hh * fac;
     if (last) {
       c.h = hh < c.h ? c.h : hnext;
@@ -811,13 +916,16 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
                  double* __restrict__ Y, long long ld, double dt, double rtol, double atol,
                  double* __restrict__ h_io, int* __restrict__ status_out,
                  int* __restrict__ attempts_out, const double* __restrict__ lnA_ext,
-                 int max_steps, double h_min, double T_min, unsigned long long* queue) {
+                 int max_steps, double h_min, double T_min, unsigned long long* queue,
+                 int* __restrict__ tape_nacc, double* __restrict__ tape_h, double* __restrict__ tape_ck,
+                 int tape_cap, int interval) {
   extern __shared__ double smem[];
   const Team tm = make_team(smem);
   long long cell = -1;
   double Pc = 0.0;
   Ctl c;
   c.done = true;
+  int nacc = 0;
   // bounded: every iteration either retires a cell or makes an attempt (<= max_steps per cell)
   for (;;) {
     if (c.done) {
@@ -834,18 +942,36 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
       c.reject_last = false;
       c.done = false;
       const bool ok = load_cell(tm, cell, T, Y, ld);
+      nacc = 0;
       if (!ok || tm.at(OFF_Y, 0) < T_min) {
         if (tm.tl == 0) {
           if (status_out) status_out[cell] = ok ? ST_SKIPPED : ST_NONFINITE;
           if (attempts_out) attempts_out[cell] = 0;
+          if (tape_nacc) tape_nacc[cell] = 0;
         }
         c.done = true;
         tsync();
         continue;
       }
+      if (tape_ck)  // checkpoint 0: the initial state
+        for (int i = tm.tl; i < NEQ; i += TEAM) tape_ck[(long long)i * n_cells + cell] = tm.at(OFF_Y, i);
     }
     ros4_advance(tm, c, Pc, dt, rtol, atol, max_steps, h_min, lnA_ext);
+    if (tape_h && c.acc) {
+      // record the accepted step; checkpoint the state after every `interval` accepted steps
+      if (nacc < tape_cap) {
+        if (tm.tl == 0) tape_h[(long long)nacc * n_cells + cell] = c.hh;
+        ++nacc;
+        if (nacc % interval == 0 && nacc < tape_cap)
+          for (int i = tm.tl; i < NEQ; i += TEAM)
+            tape_ck[((long long)(nacc / interval) * NEQ + i) * n_cells + cell] = tm.at(OFF_Y, i);
+      } else {
+        c.status = ST_TAPE_FULL;
+        c.done = true;
+      }
+    }
     if (c.done) {
+      if (tm.tl == 0 && tape_nacc) tape_nacc[cell] = nacc;
       store_cell(tm, cell, T, Y, ld);
       if (tm.tl == 0) {
         if (h_io) h_io[cell] = c.h;
@@ -953,3 +1079,575 @@ extern "C" __global__ void chem_plain_finish_k(long long n_cells, int* __restric
   }
   (void)wflags_init_status;
 }
+
+// ============================================================================ discrete adjoint
+// Gradients of a loss on the final state with respect to ln A of every reaction and to the
+// initial state, through the ROS4 steps with the accepted step sizes frozen (Sec. 2.3 algebra,
+// differentiated).  Only built for multi-lane teams (contiguous shared-memory layout), and only
+// into the separately compiled adjoint module (CHEM_ADJOINT) so that forward modules compile fast.
+#if TEAM > 1 && defined(CHEM_ADJOINT)
+
+// forward-mode dual number: value and one directional derivative
+struct DD {
+  double v, d;
+};
+__device__ __forceinline__ DD mk(double v, double d) { DD r; r.v = v; r.d = d; return r; }
+__device__ __forceinline__ DD operator+(DD a, DD b) { return mk(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ DD operator-(DD a, DD b) { return mk(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ DD operator-(DD a) { return mk(-a.v, -a.d); }
+__device__ __forceinline__ DD operator*(DD a, DD b) { return mk(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ DD operator/(DD a, DD b) {
+  const double q = a.v / b.v;
+  return mk(q, (a.d - q * b.d) / b.v);
+}
+__device__ __forceinline__ DD operator+(DD a, double b) { return mk(a.v + b, a.d); }
+__device__ __forceinline__ DD operator+(double b, DD a) { return mk(a.v + b, a.d); }
+__device__ __forceinline__ DD operator-(DD a, double b) { return mk(a.v - b, a.d); }
+__device__ __forceinline__ DD operator-(double b, DD a) { return mk(b - a.v, -a.d); }
+__device__ __forceinline__ DD operator*(DD a, double b) { return mk(a.v * b, a.d * b); }
+__device__ __forceinline__ DD operator*(double b, DD a) { return mk(a.v * b, a.d * b); }
+__device__ __forceinline__ DD operator/(DD a, double b) { return mk(a.v / b, a.d / b); }
+__device__ __forceinline__ DD operator/(double b, DD a) {
+  const double q = b / a.v;
+  return mk(q, -q * a.d / a.v);
+}
+__device__ __forceinline__ DD exp(DD a) { const double e = exp(a.v); return mk(e, e * a.d); }
+__device__ __forceinline__ DD log(DD a) { return mk(log(a.v), a.d / a.v); }
+__device__ __forceinline__ DD log10(DD a) { return mk(log10(a.v), a.d / (a.v * LN10)); }
+__device__ __forceinline__ double vof(double a) { return a; }
+__device__ __forceinline__ double vof(DD a) { return a.v; }
+__device__ __forceinline__ double dof(double a) { return 0.0; }
+__device__ __forceinline__ double dof(DD a) { return a.d; }
+template <class S> struct S_is_dual { static constexpr bool value = false; };
+template <> struct S_is_dual<DD> { static constexpr bool value = true; };
+template <class S> __device__ __forceinline__ S szero();
+template <> __device__ __forceinline__ double szero<double>() { return 0.0; }
+template <> __device__ __forceinline__ DD szero<DD>() { return mk(0.0, 0.0); }
+__device__ __forceinline__ void atomic_add_s(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_s(DD* p, DD v) {
+  atomicAdd(&p->v, v.v);
+  atomicAdd(&p->d, v.d);
+}
+__device__ __forceinline__ DD shfl_xor(DD a, int o) {
+  return mk(__shfl_xor_sync(0xffffffffu, a.v, o), __shfl_xor_sync(0xffffffffu, a.d, o));
+}
+__device__ __forceinline__ double shfl_xor(double a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+
+// adjoint slots, appended after the forward layout (units of doubles; DD arrays take 2 per entry)
+#define AOFF_LAM SLOTS
+#define AOFF_YB (AOFF_LAM + NEQ)
+#define AOFF_UB (AOFF_YB + NEQ)
+#define AOFF_W (AOFF_UB + 4 * NEQ)
+#define AOFF_FB (AOFF_W + 4 * NEQ)
+#define AOFF_Y2 (AOFF_FB + NEQ)
+#define AOFF_Y3 (AOFF_Y2 + NEQ)
+#define AOFF_V (AOFF_Y3 + NEQ)
+#define AOFF_GP (AOFF_V + NEQ)
+#define AOFF_S (AOFF_GP + NR)
+// S-typed (2 doubles each) scratch of the VJP: state, gy, C, hRT, cp, ex, iex, dcp, atilde, Cbar,
+// omega (11 x NS) and q (NR), plus 8 reduction slots
+#define VS_Y 0
+#define VS_GY (VS_Y + NEQ)
+#define VS_C (VS_GY + NEQ)
+#define VS_HRT (VS_C + NS)
+#define VS_CP (VS_HRT + NS)
+#define VS_EX (VS_CP + NS)
+#define VS_IEX (VS_EX + NS)
+#define VS_DCP (VS_IEX + NS)
+#define VS_AT (VS_DCP + NS)
+#define VS_CB (VS_AT + NS)
+#define VS_OM (VS_CB + NS)
+#define VS_Q (VS_OM + NS)
+#define VS_RED (VS_Q + NR)
+#define VS_TOTAL (VS_RED + 8 * TEAM / 32)
+#define ASLOTS (AOFF_S + 2 * VS_TOTAL)
+
+template <class S>
+__device__ __forceinline__ S team_sum_s(const Team& tm, S v, S* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = v + shfl_xor(v, o);
+#if TEAM > 32
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = red[0];
+  for (int w = 1; w < TEAM / 32; ++w) v = v + red[w];
+  __syncthreads();
+#endif
+  return v;
+}
+
+// Reverse-mode vector-Jacobian product of f at the state in VS_Y (type S):
+//   gy = J(y)^T v  (into VS_GY)  and  gp_r += v^T d f / d lnA_r  (value part when S = double,
+//   directional-derivative part when S = DD; accumulated into AOFF_GP).
+// phi(y) = v^T f(y) = sum_k atilde_k omega_k with atilde_k = V v_{1+k} [k < bath]
+// - v_T T V (h_k/RT) / cpm; gy = sum_k atilde_k d omega_k/dy + sum_k omega_k d atilde_k/dy.
+template <class S>
+__device__ void vjp(const Team& tm, double P, const double* __restrict__ lnA_ext) {
+  S* sb = reinterpret_cast<S*>(&tm.base[AOFF_S]);
+  S* Y = sb + VS_Y;
+  const double* v = &tm.base[AOFF_V];
+  double* gp = &tm.base[AOFF_GP];
+  const S T = Y[0];
+  const S invT = 1.0 / T;
+  const S lnT = log(T);
+  const S Z = szero<S>();
+  S wsum = Z, nsum = Z;
+  for (int k = tm.tl; k < NS - 1; k += TEAM) {
+    wsum = wsum + mk_W[k] * Y[1 + k];
+    nsum = nsum + Y[1 + k];
+  }
+  S* red = sb + VS_RED;
+  wsum = team_sum_s(tm, wsum, red);
+  nsum = team_sum_s(tm, nsum, red);
+  const S nb = (1.0 - wsum) * mk_invW[BATH];
+  const S V = (nsum + nb) * R_U * T / P;
+  const S invV = 1.0 / V;
+  S cpm = Z, dcpm = Z;
+  for (int k = tm.tl; k < NS; k += TEAM) {
+    const S n = k < NS - 1 ? Y[1 + k] : nb;
+    sb[VS_C + k] = n * invV;
+    const int r = vof(T) < mk_Tmid[k] ? 0 : 1;
+    const double* c = mk_cp[k][r];
+    const double* hh = mk_h[k][r];
+    const double* s = mk_s[k][r];
+    const double* d = mk_dcp[k][r];
+    const S cp = c[0] + T * (c[1] + T * (c[2] + T * (c[3] + T * c[4])));
+    const S hRT = hh[0] + T * (hh[1] + T * (hh[2] + T * (hh[3] + T * hh[4]))) + hh[5] * invT;
+    const S sR = s[0] * lnT + s[6] + T * (s[1] + T * (s[2] + T * (s[3] + T * s[4])));
+    const S dcp = d[0] + T * (d[1] + T * (d[2] + T * d[3]));
+    const S ex = exp(sR - hRT);
+    sb[VS_CP + k] = cp;
+    sb[VS_HRT + k] = hRT;
+    sb[VS_EX + k] = ex;
+    sb[VS_IEX + k] = 1.0 / ex;
+    sb[VS_DCP + k] = dcp;
+    sb[VS_CB + k] = Z;
+    cpm = cpm + n * cp;
+    dcpm = dcpm + n * dcp;
+  }
+  cpm = team_sum_s(tm, cpm, red);
+  dcpm = team_sum_s(tm, dcpm, red);
+  const double vT = v[0];
+  const S kT = vT * T * V / cpm;
+  for (int k = tm.tl; k < NS; k += TEAM) {
+    const S a0 = k < NS - 1 ? V * v[1 + k] : Z;
+    sb[VS_AT + k] = a0 - kT * sb[VS_HRT + k];
+  }
+  tsync();
+  const S Ctot = P * invT / R_U;
+  const S rtp = R_U * T / P_ATM;
+  const S irtp = 1.0 / rtp;
+  S Tbar = Z, Bbar = Z;
+  for (int r = tm.tl; r < NR; r += TEAM) {
+    const int kind = mk_kind[r];
+    const double lA = lnA_ext ? lnA_ext[r] : mk_lnA[r];
+    const S kinf = exp(lA + mk_b[r] * lnT - mk_th[r] * invT);
+    S kf = kinf;
+    S dlkf_dT = (mk_b[r] + mk_th[r] * invT) * invT;
+    S dlkf_dM = Z;
+    S M = Z;
+    S one_minus_g = Z + 1.0;  // d ln kf / d ln k_inf
+    if (kind != ELEM) {
+      M = Ctot;
+      for (int e = mk_effoff[r]; e < mk_effoff[r + 1]; ++e) M = M + mk_effval[e] * sb[VS_C + mk_effsp[e]];
+    }
+    if (kind >= LIND) {
+      const S k0 = exp(mk_lnA0[r] + mk_b0[r] * lnT - mk_th0[r] * invT);
+      S Pr = k0 * M / kinf;
+      bool floored = false;
+      if (vof(Pr) < 1e-300) { Pr = Z + 1e-300; floored = true; }
+      S F = Z + 1.0, dlF_dlPr = Z, dlF_dT = Z;
+      if (kind == TROE) {
+        const double a = mk_troe[r][0];
+        const S e3 = exp(-T * mk_troe[r][1]);
+        const S e1 = exp(-T * mk_troe[r][2]);
+        const double T2 = mk_troe[r][3];
+        const S e2 = T2 > 0.0 ? exp(-T2 * invT) : Z;
+        const S Fc = (1.0 - a) * e3 + a * e1 + e2;
+        const S lFc = log10(Fc);
+        const S c = -0.4 - 0.67 * lFc;
+        const S n = 0.75 - 1.27 * lFc;
+        const S x = log10(Pr) + c;
+        const S d = n - 0.14 * x;
+        const S id = 1.0 / d;
+        const S f1 = x * id;
+        const S den = 1.0 / (1.0 + f1 * f1);
+        const S lF = lFc * den;
+        F = exp(lF * LN10);
+        const S g2 = 2.0 * lFc * f1 * den * den;
+        if (!floored) dlF_dlPr = -g2 * n * id * id;
+        const S dFc = -(1.0 - a) * mk_troe[r][1] * e3 - a * mk_troe[r][2] * e1 +
+                      (T2 > 0.0 ? T2 * invT * invT * e2 : Z);
+        const S df1_dlFc = (-0.67 * n + 1.27 * x) * id * id;
+        dlF_dT = (den - g2 * df1_dlFc) * dFc / Fc;
+      }
+      kf = kinf * (Pr / (1.0 + Pr)) * F;
+      const S g = floored ? Z : 1.0 / (1.0 + Pr) + dlF_dlPr;
+      const S dlk0 = (mk_b0[r] + mk_th0[r] * invT) * invT;
+      dlkf_dM = g / M;
+      dlkf_dT = dlkf_dT + g * (dlk0 - dlkf_dT) + dlF_dT;
+      one_minus_g = 1.0 - g;
+    }
+    S kr = kf, fwd = kf, rev = Z + 1.0;
+    const int nre = mk_nre[r], npr = mk_npr[r];
+    S abar = Z;
+    S dlKc = Z - (double)mk_dnu[r];
+    for (int i = 0; i < nre; ++i) {
+      const int sp = mk_rsp[r][i];
+      for (int q = 0; q < mk_rnu[r][i]; ++q) { fwd = fwd * sb[VS_C + sp]; kr = kr * sb[VS_EX + sp]; }
+      abar = abar - mk_rnu[r][i] * sb[VS_AT + sp];
+      dlKc = dlKc - mk_rnu[r][i] * sb[VS_HRT + sp];
+    }
+    for (int i = 0; i < npr; ++i) {
+      const int sp = mk_psp[r][i];
+      for (int q = 0; q < mk_pnu[r][i]; ++q) { rev = rev * sb[VS_C + sp]; kr = kr * sb[VS_IEX + sp]; }
+      abar = abar + mk_pnu[r][i] * sb[VS_AT + sp];
+      dlKc = dlKc + mk_pnu[r][i] * sb[VS_HRT + sp];
+    }
+    const int dnu = mk_dnu[r];
+    for (int q = 0; q < dnu; ++q) kr = kr * rtp;
+    for (int q = 0; q < -dnu; ++q) kr = kr * irtp;
+    rev = rev * kr;
+    const S m = kind == THIRD ? M : Z + 1.0;
+    const S qnet = fwd - rev;
+    const S q = m * qnet;
+    sb[VS_Q + r] = q;
+    // parameter: d q / d lnA_r = q (d ln kf / d ln k_inf)
+    const S gpr = abar * q * one_minus_g;
+    gp[r] += S_is_dual<S>::value ? dof(gpr) : vof(gpr);
+    dlKc = dlKc * invT;
+    const S dqdT = m * (fwd * dlkf_dT - rev * (dlkf_dT - dlKc));
+    Tbar = Tbar + abar * dqdT;
+    if (kind != ELEM) {
+      const S beta = kind == THIRD ? qnet : qnet * dlkf_dM;
+      Bbar = Bbar + abar * beta;
+      for (int e = mk_effoff[r]; e < mk_effoff[r + 1]; ++e)
+        atomic_add_s(&sb[VS_CB + mk_effsp[e]], abar * beta * mk_effval[e]);
+    }
+    // d q / d C_j of the mass-action products
+    for (int i = 0; i < nre; ++i) {
+      const int nu = mk_rnu[r][i];
+      S p = m * kf * (double)nu;
+      for (int i2 = 0; i2 < nre; ++i2) {
+        const int e = i2 == i ? nu - 1 : mk_rnu[r][i2];
+        for (int t = 0; t < e; ++t) p = p * sb[VS_C + mk_rsp[r][i2]];
+      }
+      atomic_add_s(&sb[VS_CB + mk_rsp[r][i]], abar * p);
+    }
+    for (int i = 0; i < npr; ++i) {
+      const int nu = mk_pnu[r][i];
+      S p = -(m * kr * (double)nu);
+      for (int i2 = 0; i2 < npr; ++i2) {
+        const int e = i2 == i ? nu - 1 : mk_pnu[r][i2];
+        for (int t = 0; t < e; ++t) p = p * sb[VS_C + mk_psp[r][i2]];
+      }
+      atomic_add_s(&sb[VS_CB + mk_psp[r][i]], abar * p);
+    }
+  }
+  Tbar = team_sum_s(tm, Tbar, red);
+  Bbar = team_sum_s(tm, Bbar, red);
+  tsync();
+  // omega from q (fixed-order gather), and the mixture sums that use it
+  S Q = Z, cpw = Z, vw = Z, Dbar = Z;
+  for (int k = tm.tl; k < NS; k += TEAM) {
+    S om = Z;
+    for (int sg = mk_spseg_beg[k]; sg < mk_spseg_beg[k + 1]; ++sg)
+      for (int e = mk_gseg_beg[sg]; e < mk_gseg_beg[sg + 1]; ++e) om = om + mk_gent_nu[e] * sb[VS_Q + mk_gent_rx[e]];
+    sb[VS_OM + k] = om;
+    Q = Q + sb[VS_HRT + k] * om;
+    cpw = cpw + sb[VS_CP + k] * om;
+    if (k < NS - 1) vw = vw + v[1 + k] * om;
+    const S cb = sb[VS_CB + k] + Bbar;  // default third-body efficiency part on every C_j
+    sb[VS_CB + k] = cb;
+    Dbar = Dbar + cb * sb[VS_C + k];
+  }
+  Q = team_sum_s(tm, Q, red);
+  cpw = team_sum_s(tm, cpw, red);
+  vw = team_sum_s(tm, vw, red);
+  Dbar = team_sum_s(tm, Dbar, red);
+  tsync();
+  const S Sp = vw - vT * T * Q / cpm;  // sum_k omega_k atilde_k / V
+  const S RTP = R_U * T / P;
+  const S icpm2 = 1.0 / (cpm * cpm);
+  S* gy = sb + VS_GY;
+  if (tm.tl == 0)
+    gy[0] = Tbar - Dbar * invT + V * invT * Sp - vT * V * (cpw / cpm - T * Q * dcpm * icpm2);
+  const S cbb = sb[VS_CB + BATH];
+  const S cpb = sb[VS_CP + BATH];
+  for (int j = tm.tl; j < NS - 1; j += TEAM) {
+    const double w = mk_wratio[j];
+    gy[1 + j] = (sb[VS_CB + j] - w * cbb) * invV - Dbar * RTP * (1.0 - w) * invV + RTP * (1.0 - w) * Sp +
+                vT * T * V * Q * (sb[VS_CP + j] - w * cpb) * icpm2;
+  }
+  tsync();
+}
+
+// Solve M^T x = b in place at slot ob with the LU of P M (P M = L U, so M^T = U^T L^T P):
+// U^T z = b forward, L^T t = z backward, x = P^T t.  The first warp works.
+__device__ void lu_solve_T(const Team& tm, int ob) {
+  if (tm.tl < 32) {
+    const int ln = tm.tl;
+    for (int i = ln; i < NEQ; i += 32) tm.at(OFF_TMP, i) = tm.at(ob, i);
+    __syncwarp();
+    for (int i = 0; i < NEQ; ++i) {
+      const double zi = tm.at(OFF_TMP, i) * tm.at(OFF_INVD, i);
+      __syncwarp();
+      if (ln == (i & 31)) tm.at(OFF_TMP, i) = zi;
+      for (int k = i + 1 + ln; k < NEQ; k += 32) tm.at(OFF_TMP, k) -= tm.A(i, k) * zi;
+      __syncwarp();
+    }
+    for (int i = NEQ - 1; i > 0; --i) {
+      const double ti = tm.at(OFF_TMP, i);
+      for (int k = ln; k < i; k += 32) tm.at(OFF_TMP, k) -= tm.A(i, k) * ti;
+      __syncwarp();
+    }
+    for (int i = ln; i < NEQ; i += 32) tm.at(ob, tm.perm(i)) = tm.at(OFF_TMP, i);
+  }
+  tsync();
+}
+
+// VJP at the state in slot oy (double) with weights at AOFF_V; gy added to yb scaled by the
+// coefficients of up to three destinations: dst[0] += c0 gy, ...
+template <class S>
+__device__ __forceinline__ void set_vjp_state(const Team& tm, int oy, int odir) {
+  S* sb = reinterpret_cast<S*>(&tm.base[AOFF_S]);
+  for (int i = tm.tl; i < NEQ; i += TEAM) {
+    S v;
+    if constexpr (S_is_dual<S>::value) v = mk(tm.at(oy, i), tm.at(odir, i));
+    else v = tm.at(oy, i);
+    sb[VS_Y + i] = v;
+  }
+  tsync();
+}
+
+__device__ __forceinline__ void add_gy(const Team& tm, bool dual, int o1, double c1, int o2, double c2, int o3, double c3) {
+  for (int i = tm.tl; i < NEQ; i += TEAM) {
+    double g;
+    if (dual) g = reinterpret_cast<const DD*>(&tm.base[AOFF_S])[VS_GY + i].d;
+    else g = reinterpret_cast<const double*>(&tm.base[AOFF_S])[VS_GY + i];
+    if (o1 >= 0) tm.at(o1, i) += c1 * g;
+    if (o2 >= 0) tm.at(o2, i) += c2 * g;
+    if (o3 >= 0) tm.at(o3, i) += c3 * g;
+  }
+  tsync();
+}
+
+// Adjoint of one frozen-h ROS4 step y_n -> y_{n+1}: on entry OFF_Y = y_n and AOFF_LAM =
+// dL/dy_{n+1}; on exit AOFF_LAM = dL/dy_n, and dL/dlnA accumulated in AOFF_GP.
+// Forward: M = I/(gamma h) - J(y), u_i = M^-1 r_i, r_1 = f(y), r_2 = f(Y2) + c21/h u1,
+// r_3 = f(Y3) + (c31 u1 + c32 u2)/h, r_4 = f(Y3) + (c41 u1 + c42 u2 + c43 u3)/h,
+// Y2 = y + a21 u1, Y3 = y + a31 u1 + a32 u2, y_{n+1} = y + sum m_i u_i.
+// Reverse: ubar_i = m_i lambda, w_i = M^-T ubar_i (taken in the order 4, 3, 2, 1 as each ubar_i
+// becomes final), fbar pulls back through J(Y)^T and d f / d lnA (VJP), and M's dependence on
+// J(y) adds sum_i d/dy [w_i^T J(y) u_i] and d/dlnA [w_i^T J(y) u_i] (dual-number VJPs at y along
+// u_i with weights w_i).
+__device__ void adjoint_step(const Team& tm, double P, double h, const double* lnA_ext) {
+  const int U1 = OFF_U, U2 = OFF_U + NEQ, U3 = OFF_U + 2 * NEQ, U4 = OFF_U + 3 * NEQ;
+  const int W1 = AOFF_W, W2 = AOFF_W + NEQ, W3 = AOFF_W + 2 * NEQ, W4 = AOFF_W + 3 * NEQ;
+  const int B1 = AOFF_UB, B2 = AOFF_UB + NEQ, B3 = AOFF_UB + 2 * NEQ, B4 = AOFF_UB + 3 * NEQ;
+  const double ih = 1.0 / h;
+  // ---- forward recompute
+  eval_f_jac(tm, OFF_Y, U1, P, lnA_ext, -1.0, 1.0 / (RGAM * h));
+  lu_factor(tm);
+  lu_solve(tm, U1);
+  for (int i = tm.tl; i < NEQ; i += TEAM) {
+    const double v = tm.at(OFF_Y, i) + RA21 * tm.at(U1, i);
+    tm.at(OFF_YT, i) = v;
+    tm.at(AOFF_Y2, i) = v;
+  }
+  tsync();
+  eval_f(tm, OFF_YT, OFF_F, P, lnA_ext);
+  for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(U2, i) = tm.at(OFF_F, i) + (RC21 * ih) * tm.at(U1, i);
+  tsync();
+  lu_solve(tm, U2);
+  for (int i = tm.tl; i < NEQ; i += TEAM) {
+    const double v = tm.at(OFF_Y, i) + RA31 * tm.at(U1, i) + RA32 * tm.at(U2, i);
+    tm.at(OFF_YT, i) = v;
+    tm.at(AOFF_Y3, i) = v;
+  }
+  tsync();
+  eval_f(tm, OFF_YT, OFF_F, P, lnA_ext);
+  for (int i = tm.tl; i < NEQ; i += TEAM)
+    tm.at(U3, i) = tm.at(OFF_F, i) + (RC31 * ih) * tm.at(U1, i) + (RC32 * ih) * tm.at(U2, i);
+  tsync();
+  lu_solve(tm, U3);
+  for (int i = tm.tl; i < NEQ; i += TEAM)
+    tm.at(U4, i) = tm.at(OFF_F, i) + (RC41 * ih) * tm.at(U1, i) + (RC42 * ih) * tm.at(U2, i) +
+                   (RC43 * ih) * tm.at(U3, i);
+  tsync();
+  lu_solve(tm, U4);
+  // ---- reverse
+  for (int i = tm.tl; i < NEQ; i += TEAM) {
+    const double l = tm.at(AOFF_LAM, i);
+    tm.at(AOFF_YB, i) = l;
+    tm.at(B1, i) = RM1 * l;
+    tm.at(B2, i) = RM2 * l;
+    tm.at(B3, i) = RM3 * l;
+    tm.at(B4, i) = RM4 * l;
+  }
+  tsync();
+  // stage 4
+  for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(W4, i) = tm.at(B4, i);
+  tsync();
+  lu_solve_T(tm, W4);
+  for (int i = tm.tl; i < NEQ; i += TEAM) {
+    const double w = tm.at(W4, i);
+    tm.at(AOFF_FB, i) = w;
+    tm.at(B1, i) += (RC41 * ih) * w;
+    tm.at(B2, i) += (RC42 * ih) * w;
+    tm.at(B3, i) += (RC43 * ih) * w;
+  }
+  tsync();
+  // stage 3
+  for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(W3, i) = tm.at(B3, i);
+  tsync();
+  lu_solve_T(tm, W3);
+  for (int i = tm.tl; i < NEQ; i += TEAM) {
+    const double w = tm.at(W3, i);
+    tm.at(AOFF_FB, i) += w;
+    tm.at(AOFF_V, i) = tm.at(AOFF_FB, i);
+    tm.at(B1, i) += (RC31 * ih) * w;
+    tm.at(B2, i) += (RC32 * ih) * w;
+  }
+  tsync();
+  set_vjp_state<double>(tm, AOFF_Y3, AOFF_Y3);
+  vjp<double>(tm, P, lnA_ext);
+  add_gy(tm, false, AOFF_YB, 1.0, B1, RA31, B2, RA32);
+  // stage 2
+  for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(W2, i) = tm.at(B2, i);
+  tsync();
+  lu_solve_T(tm, W2);
+  for (int i = tm.tl; i < NEQ; i += TEAM) {
+    const double w = tm.at(W2, i);
+    tm.at(AOFF_V, i) = w;
+    tm.at(B1, i) += (RC21 * ih) * w;
+  }
+  tsync();
+  set_vjp_state<double>(tm, AOFF_Y2, AOFF_Y2);
+  vjp<double>(tm, P, lnA_ext);
+  add_gy(tm, false, AOFF_YB, 1.0, B1, RA21, -1, 0.0);
+  // stage 1
+  for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(W1, i) = tm.at(B1, i);
+  tsync();
+  lu_solve_T(tm, W1);
+  for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(AOFF_V, i) = tm.at(W1, i);
+  tsync();
+  set_vjp_state<double>(tm, OFF_Y, OFF_Y);
+  vjp<double>(tm, P, lnA_ext);
+  add_gy(tm, false, AOFF_YB, 1.0, -1, 0.0, -1, 0.0);
+  // M = I/(gamma h) - J(y): second-order terms along each u_i with weights w_i
+  for (int st = 0; st < 4; ++st) {
+    for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(AOFF_V, i) = tm.at(AOFF_W + st * NEQ, i);
+    tsync();
+    set_vjp_state<DD>(tm, OFF_Y, OFF_U + st * NEQ);
+    vjp<DD>(tm, P, lnA_ext);
+    add_gy(tm, true, AOFF_YB, 1.0, -1, 0.0, -1, 0.0);
+  }
+  for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(AOFF_LAM, i) = tm.at(AOFF_YB, i);
+  tsync();
+}
+
+__device__ __forceinline__ long long team_global_id() {
+  return (long long)blockIdx.x * NTEAM + (TEAM == 32 ? (threadIdx.x >> 5) : 0);
+}
+
+// Reverse sweep over every cell's checkpointed forward: per cell, segments of `interval`
+// accepted steps are recomputed from their checkpoint (states kept in this team's slice of
+// `seg`), then stepped through backwards.  dL/dlnA is accumulated per team and written to
+// gp_partial[team][r]; chem_adjoint_reduce_k sums the teams in a fixed order.
+extern "C" __global__ void __launch_bounds__(TPB)
+chem_adjoint_k(long long n_cells, const double* __restrict__ P, const double* __restrict__ gT,
+               const double* __restrict__ gY, long long ld, double* __restrict__ gT0,
+               double* __restrict__ gY0, const double* __restrict__ lnA_ext,
+               const int* __restrict__ tape_nacc, const double* __restrict__ tape_h,
+               const double* __restrict__ tape_ck, int interval, double* __restrict__ seg,
+               double* __restrict__ gp_partial, unsigned long long* queue) {
+  extern __shared__ double smem[];
+  const Team tm = make_team(smem);
+  const long long tg = team_global_id();
+  for (int r = tm.tl; r < NR; r += TEAM) tm.at(AOFF_GP, r) = 0.0;
+  tsync();
+  double* segc = seg + tg * (long long)interval * NEQ;
+  for (;;) {
+    long long nc = 0;
+    if (tm.tl == 0) nc = (long long)atomicAdd(queue, 1ULL);
+    const long long cell = team_bcast_ll(tm, nc);
+    if (cell >= n_cells) break;
+    const int nacc = tape_nacc[cell];
+    const double Pc = P[cell];
+    const double gb = gY[(long long)BATH * ld + cell];
+    if (tm.tl == 0) tm.at(AOFF_LAM, 0) = gT[cell];
+    for (int k = tm.tl; k < NS - 1; k += TEAM) tm.at(AOFF_LAM, 1 + k) = mk_W[k] * (gY[k * ld + cell] - gb);
+    tsync();
+    for (int sg = (nacc - 1) / interval; nacc > 0 && sg >= 0; --sg) {
+      const int s0 = sg * interval;
+      const int s1 = min(nacc, s0 + interval);
+      for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(OFF_Y, i) = tape_ck[((long long)sg * NEQ + i) * n_cells + cell];
+      tsync();
+      for (int s = s0; s < s1; ++s) {
+        for (int i = tm.tl; i < NEQ; i += TEAM) segc[(s - s0) * NEQ + i] = tm.at(OFF_Y, i);
+        if (s + 1 < s1) {
+          ros4_attempt(tm, Pc, tape_h[(long long)s * n_cells + cell], 1.0, 1.0, lnA_ext);
+          for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(OFF_Y, i) = tm.at(OFF_YT, i);
+        }
+        tsync();
+      }
+      for (int s = s1 - 1; s >= s0; --s) {
+        for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(OFF_Y, i) = segc[(s - s0) * NEQ + i];
+        tsync();
+        adjoint_step(tm, Pc, tape_h[(long long)s * n_cells + cell], lnA_ext);
+      }
+    }
+    // initial state y0 = [T0, Y0_k / W_k]; the bath mass fraction does not enter y0
+    if (tm.tl == 0) {
+      gT0[cell] = tm.at(AOFF_LAM, 0);
+      gY0[(long long)BATH * ld + cell] = 0.0;
+    }
+    for (int k = tm.tl; k < NS - 1; k += TEAM) gY0[k * ld + cell] = tm.at(AOFF_LAM, 1 + k) * mk_invW[k];
+    tsync();
+  }
+  for (int r = tm.tl; r < NR; r += TEAM) gp_partial[tg * NR + r] = tm.at(AOFF_GP, r);
+}
+
+extern "C" __global__ void chem_adjoint_reduce_k(long long n_parts, const double* __restrict__ gp_partial,
+                                                 double* __restrict__ g_lnA) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= NR) return;
+  double s = 0.0;
+  for (long long t = 0; t < n_parts; ++t) s += gp_partial[t * NR + r];
+  g_lnA[r] = s;
+}
+
+// Vector-Jacobian products per cell (parity entry point of the adjoint's building block):
+// gy = J(y)^T v  [NEQ x ld], gp = (d f / d lnA)^T v  [NR x ld].
+extern "C" __global__ void __launch_bounds__(TPB)
+chem_eval_vjp_k(long long n_cells, const double* __restrict__ T, const double* __restrict__ P,
+                const double* __restrict__ n, const double* __restrict__ v, double* __restrict__ gy,
+                double* __restrict__ gp, long long ld, const double* __restrict__ lnA_ext) {
+  extern __shared__ double smem[];
+  const Team tm = make_team(smem);
+  const long long stride = (long long)gridDim.x * NTEAM;
+  for (long long c = team_global_id(); c < n_cells; c += stride) {
+    if (tm.tl == 0) tm.at(OFF_Y, 0) = T[c];
+    for (int k = tm.tl; k < NS - 1; k += TEAM) tm.at(OFF_Y, 1 + k) = n[k * ld + c];
+    for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(AOFF_V, i) = v[i * ld + c];
+    for (int r = tm.tl; r < NR; r += TEAM) tm.at(AOFF_GP, r) = 0.0;
+    tsync();
+    set_vjp_state<double>(tm, OFF_Y, OFF_Y);
+    vjp<double>(tm, P[c], lnA_ext);
+    const double* g = reinterpret_cast<const double*>(&tm.base[AOFF_S]) + VS_GY;
+    for (int i = tm.tl; i < NEQ; i += TEAM) gy[i * ld + c] = g[i];
+    for (int r = tm.tl; r < NR; r += TEAM) gp[(long long)r * ld + c] = tm.at(AOFF_GP, r);
+    tsync();
+  }
+}
+
+#endif  // TEAM > 1 && CHEM_ADJOINT
+
+extern "C" __device__ const int chem_aslots =
+#if TEAM > 1 && defined(CHEM_ADJOINT)
+    ASLOTS;
+#else
+    0;
+#endif
