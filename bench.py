@@ -151,27 +151,146 @@ def fp64_peak_tflops(torch, dev):
 
 
 def cpu_oracle_rate(path, wl, budget_s=15.0, max_cells=4096):
-    """Oracle cells/s on the host cores on a bounded sample of the workload."""
+    """Oracle cells/s (cells x split steps per second) on the host cores, on a bounded, evenly
+    strided sample of the workload.  For the flame-front workload the oracle relaxes its own
+    product templates first (as the GPU leg does), untimed."""
     from oracle import oracle as O
     from paper_2205_05681_gb300 import synth
-    mech_name, n_cells, recipe, seed, dt, _ = synth.WORKLOADS[wl]
+    mech_name, n_cells, recipe, seed, dt, splits = synth.WORKLOADS[wl]
     om = O.Mechanism(path)
     st = synth.make_states(synth.mechanism(mech_name), n_cells, recipe, seed)
     cores = os.cpu_count() or 1
+
+    def sample_states(idx):
+        y = om.state_from_TY(st.T[idx], st.Y[idx])
+        if recipe == "ch4_front":
+            prod = np.where(st.T[idx] >= 1500.0)[0]
+            if len(prod):
+                k = min(8, len(prod))
+                yt, _ = om.integrate(y[prod[:k]], st.P[idx][prod[:k]], 1e-3, threads=cores)
+                y[prod] = yt[np.arange(len(prod)) % k]
+        return y
+
+    def run(idx, y):
+        hh = np.zeros(len(idx))
+        for _ in range(splits):
+            y, info = om.integrate(y, st.P[idx], dt, h=hh, threads=cores)
+            hh = info["h"]
+        return y
+
     # calibrate on a small sample, then size the timed sample to ~budget_s
     idx = np.arange(0, n_cells, max(1, n_cells // (2 * cores)))[: 2 * cores]
-    y = om.state_from_TY(st.T[idx], st.Y[idx])
+    y = sample_states(idx)
     t0 = time.perf_counter()
-    om.integrate(y, st.P[idx], dt, threads=cores)
+    run(idx, y)
     per = (time.perf_counter() - t0) / len(idx)
     ns = int(min(max_cells, max(len(idx), budget_s / max(per, 1e-9))))
     idx = np.linspace(0, n_cells - 1, ns).astype(int)
-    y = om.state_from_TY(st.T[idx], st.Y[idx])
+    y = sample_states(idx)
     t0 = time.perf_counter()
-    om.integrate(y, st.P[idx], dt, threads=cores)
+    run(idx, y)
     el = time.perf_counter() - t0
-    return ns / el, cores, "%d of %d cells (evenly strided), %.1f s on %d host threads" % (
-        ns, n_cells, el, cores)
+    return ns * splits / el, cores, "%d of %d cells (evenly strided) x %d split steps, %.1f s on %d host threads" % (
+        ns, n_cells, splits, el, cores)
+
+
+def relax_products(m, st, T0, P, Y0, torch, np, n_templates=1024, t_relax=1e-3):
+    """Near-equilibrium cells of the flame-front workload: 1,024 template product states are
+    relaxed on the GPU for 1e-3 s (input preparation, untimed) and tiled over the product cells
+    with a 1e-9 relative perturbation of the mass fractions."""
+    front = st.T < 1500.0
+    idx = np.where(~front)[0]
+    if len(idx) == 0:
+        return {}
+    k = min(n_templates, len(idx))
+    tid = idx[:k]
+    Tt, Pt = T0[tid].clone(), P[tid].clone()
+    Yt = Y0[:, tid].clone().contiguous()
+    t0 = time.perf_counter()
+    m.integrate(Tt.contiguous(), Pt.contiguous(), Yt, t_relax)
+    torch.cuda.synchronize()
+    rel_s = time.perf_counter() - t0
+    src = torch.tensor(np.arange(len(idx)) % k, device=T0.device)
+    dst = torch.tensor(idx, device=T0.device)
+    rng = np.random.default_rng(12)
+    noise = torch.tensor(1.0 + 1e-9 * rng.standard_normal((Y0.shape[0], len(idx))), device=T0.device)
+    T0[dst] = Tt[src]
+    P[dst] = Pt[src]
+    Ynew = Yt[:, src] * noise
+    Y0[:, dst] = Ynew / Ynew.sum(0, keepdim=True)
+    return {"relaxed_templates": k, "relax_time_s": t_relax, "relax_wall_s": rel_s,
+            "front_cells": int(front.sum()), "product_cells": int(len(idx))}
+
+
+def adjoint_leg(chem, synth, torch, np, dev, path53):
+    """Checkpointed forward + discrete adjoint on the 53-species ignition workload (16,384 cells,
+    1e-4 s): loss = sum (T - T_target)^2 with T_target from a seeded ln A perturbation + noise;
+    times the taped forward, the plain forward and the reverse sweep (CUDA events)."""
+    mech_name, n, recipe, seed, dt, _ = synth.WORKLOADS["ch4_53_adjoint"]
+    st = synth.make_states(synth.mechanism(mech_name), n, recipe, seed)
+    m = chem.Mechanism(synth.mechanism_file(mech_name, MECH_DIR))
+    T0 = torch.tensor(st.T, device=dev)
+    P = torch.tensor(st.P, device=dev)
+    Y0 = torch.tensor(np.ascontiguousarray(st.Y.T), device=dev)
+    rng = np.random.default_rng(seed)
+    lnA = torch.tensor(m.lnA(), device=dev)
+    lnA_t = lnA + torch.tensor(rng.normal(0.0, 0.1, m.nr), device=dev)
+    Tt, Yt = T0.clone(), Y0.clone()
+    m.integrate(Tt, P, Yt, dt, opts=m.opts(lnA=lnA_t))
+    T_target = Tt + torch.tensor(rng.normal(0.0, 1.0, n), device=dev)
+    interval, cap = 16, 4096
+    tape = m.make_tape(n, cap, interval, device=dev)
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    res = {}
+    for rep in range(2):
+        T, Y = T0.clone(), Y0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = ev()
+        e0.record()
+        m.integrate_ckpt(T, P, Y, dt, tape, status=status, opts=m.opts(lnA=lnA))
+        e1.record()
+        e1.synchronize()
+        t_fwd = e0.elapsed_time(e1)
+        gT = 2.0 * (T - T_target)
+        gY = torch.zeros_like(Y)
+        e0, e1 = ev()
+        e0.record()
+        g_lnA, gT0, gY0 = m.adjoint(P, gT, gY, tape, opts=m.opts(lnA=lnA))
+        e1.record()
+        e1.synchronize()
+        t_adj = e0.elapsed_time(e1)
+        T2, Y2 = T0.clone(), Y0.clone()
+        e0, e1 = ev()
+        e0.record()
+        m.integrate(T2, P, Y2, dt, opts=m.opts(lnA=lnA))
+        e1.record()
+        e1.synchronize()
+        t_plain = e0.elapsed_time(e1)
+        res = {"workload": "ch4_53_adjoint", "cells": n, "dt_s": dt, "interval": interval,
+               "fwd_ckpt_ms": t_fwd, "fwd_ms": t_plain, "adjoint_ms": t_adj,
+               "adjoint_over_fwd": t_adj / t_plain, "tape_bytes": int(tape.buf.numel()),
+               "accepted_mean": float(tape.n_accepted().float().mean().item()),
+               "ok_cells": int((status == 0).sum().item()),
+               "loss": float(((T - T_target) ** 2).sum().item()),
+               "grad_lnA_norm": float(g_lnA.norm().item())}
+    return res
+
+
+def reduce_max_seconds(sec, world, device=None):
+    """Max of the per-rank step time over all ranks (the slowest replica sets the job time)."""
+    if world == 1:
+        return sec
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([sec], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_value(cells_per_rank, splits, world, sec):
+    """Whole-job throughput: every rank integrates its own replica of the workload."""
+    return cells_per_rank * splits * world / sec
 
 
 def dist_env():
@@ -226,6 +345,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--cells", type=int, default=0,
                     help="use only the first CELLS cells of the workload (small profiling runs)")
+    ap.add_argument("--autotune", action="store_true", help="pick (team, block) on a sample first")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -252,6 +373,9 @@ def main():
     T0 = torch.tensor(st.T, device=dev)
     P = torch.tensor(st.P, device=dev)
     Y0 = torch.tensor(np.ascontiguousarray(st.Y.T), device=dev)
+    prep = {}
+    if recipe == "ch4_front":
+        prep = relax_products(m, st, T0, P, Y0, torch, np)
     T, Y = T0.clone(), Y0.clone()
     h = torch.zeros(n_cells, dtype=torch.float64, device=dev)
     status = torch.zeros(n_cells, dtype=torch.int32, device=dev)
@@ -267,8 +391,41 @@ def main():
         h.zero_()
         flush.fill_(1.0)  # evict the inputs from L2 (512 MiB > 129 MB)
 
-    def one_step(o=opts, w=ws):
+    tuned = None
+    if args.autotune:
+        tuned = m.autotune(T0, P, Y0, dt)
+        opts = m.opts(attempts=att)
+    att_total = torch.zeros(n_cells, dtype=torch.int32, device=dev)
+
+    def one_split(o=opts, w=ws):
         m.integrate(T, P, Y, dt, rtol=1e-6, atol=1e-10, h=h, status=status, opts=o, workspace=w)
+
+    graph = None
+    if splits > 1:
+        # consecutive split steps (h carried) captured once as a CUDA graph and replayed
+        def splits_body():
+            att_total.zero_()
+            for _ in range(splits):
+                one_split()
+                att_total.add_(att)
+
+        restore()
+        s_cap = torch.cuda.Stream()
+        s_cap.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s_cap):
+            splits_body()  # eager run on the capture stream before capture
+        torch.cuda.current_stream().wait_stream(s_cap)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            splits_body()
+
+        def one_step(o=opts, w=ws):
+            graph.replay()
+    else:
+        def one_step(o=opts, w=ws):
+            one_split(o, w)
+            att_total.copy_(att)
 
     for _ in range(args.warmup):
         restore()
@@ -290,13 +447,9 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    sec = sum(times) / len(times)
-    if world > 1:
-        t = torch.tensor([sec], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = t.item()
-    value = n_cells * world / sec
-    attempts = att.cpu().numpy()
+    sec = reduce_max_seconds(sum(times) / len(times), world, dev)
+    value = whole_job_value(n_cells, splits, world, sec)
+    attempts = att_total.cpu().numpy()
     st_ok = int((status.cpu().numpy() == 0).sum())
 
     # end to end: host arrays through chem_integrate_host (copies inside the timed region)
@@ -306,7 +459,7 @@ def main():
     hh = np.zeros(n_cells)
     sh = np.zeros(n_cells, dtype=np.int32)
     e2e_t = []
-    for i in range(0 if args.no_e2e else max(1, min(args.steps, 3)) + 1):
+    for i in range(0 if (args.no_e2e or splits > 1) else max(1, min(args.steps, 3)) + 1):
         Th[:] = st.T
         Yh[:] = st.Y.T
         hh[:] = 0
@@ -320,7 +473,7 @@ def main():
 
     # plain one-launch-per-attempt kernel on the same inputs
     plain = None
-    if not args.no_plain:
+    if not args.no_plain and splits == 1:
         po = m.opts(mode=chem.MODE_PLAIN)
         pws = m.workspace(n_cells, po, device=dev)
         pt = []
@@ -337,6 +490,10 @@ def main():
         plain = {"value": n_cells / pt[0], "unit": "cells/s", "ms_per_step": pt[0] * 1e3,
                  "speedup_of_persistent": pt[0] / sec}
         del pws
+
+    adjoint = None
+    if not args.no_adjoint and splits == 1 and wl == "ch4_53_fwd" and not args.cells:
+        adjoint = adjoint_leg(chem, synth, torch, np, dev, m.spec_path if hasattr(m, "spec_path") else path)
 
     if rank != 0:
         if world > 1:
@@ -362,6 +519,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl, "mechanism": mech_name, "species": N,
                    "reactions": len(spec["reactions"]), "cells": n_cells, "dt_s": dt,
+                   "split_steps_per_step": splits,
+                   "cuda_graph": splits > 1,
                    "rtol": 1e-6, "atol": 1e-10, "l2": "flushed (512 MiB write) between steps",
                    "team": cfg["team"], "block": cfg["block"], "smem_bytes": cfg["smem"],
                    "regs": cfg["regs"], "parallelism": "replicas" if world > 1 else "single"},
@@ -375,11 +534,14 @@ def main():
                      "p99": float(np.percentile(attempts, 99)), "max": int(attempts.max()),
                      "ok_cells": st_ok},
         "plain_gpu": plain,
+        "adjoint": adjoint,
+        "autotuned": tuned,
+        "input_prep": prep or None,
         "e2e": {"value": n_cells / e2e_sec, "unit": "cells/s",
                 "h2d_bytes_per_step": int(8 * n_cells * (2 + N + 1)),
                 "d2h_bytes_per_step": int(8 * n_cells * (1 + N + 1) + 4 * n_cells)},
         "cpu_baseline": cpu,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * splits,
         "clocks": clk.summary(),
         "mech_load_s": load_s,
     }

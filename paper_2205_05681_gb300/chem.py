@@ -331,6 +331,13 @@ class Tape:
         import torch
         return self.buf[: 4 * self.n_cells].view(torch.int32)
 
+    def step_sizes(self):
+        """Accepted step sizes, float64 [capacity, n_cells] view (layout of chem_tape_bytes)."""
+        import torch
+        off = (4 * self.n_cells + 255) // 256 * 256
+        n = 8 * self.n_cells * self.capacity
+        return self.buf[off: off + n].view(torch.float64).view(self.capacity, self.n_cells)
+
 
 def chem_integrate_fn():
     """torch.autograd.Function: (T0 [C], Y0 [Ns, C], lnA [Nr]) -> (T [C], Y [Ns, C]) with

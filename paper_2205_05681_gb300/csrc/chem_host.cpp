@@ -518,31 +518,17 @@ struct chem_mech {
 
 namespace {
 
-int n_segments(const MechData& m) {
-  const int ns = (int)m.sp.size();
-  int nseg = 0;
-  for (int k = 0; k < ns; ++k) {
-    size_t cnt = 0;
-    for (auto& x : m.rx) {
-      int nu = 0;
-      for (int i = 0; i < x.npr; ++i) if (x.psp[i] == k) nu += x.pnu[i];
-      for (int i = 0; i < x.nre; ++i) if (x.rsp[i] == k) nu -= x.rnu[i];
-      if (nu) ++cnt;
-    }
-    nseg += (int)((cnt + kSegLen - 1) / kSegLen);
-  }
-  return std::max(nseg, 1);
-}
-
 // shared-memory slots of one cell; mirrors the OFF_* layout of ros4_device.cuh
 int slots_for(const MechData& m) {
   const int ns = (int)m.sp.size(), nr = (int)m.rx.size();
-  return ns * ns + 23 * ns + nr + n_segments(m) + 16;
+  (void)nr;
+  return ns * ns + 17 * ns + 16;
 }
 
+// default kernel configuration by mechanism size (the autotuner's usual pick on GB300):
+// two warps per cell up to 64 species, eight warps per cell above
 void default_config(int ns, int* team, int* tpb) {
-  if (ns <= 24) { *team = 32; *tpb = 128; }
-  else if (ns <= 64) { *team = 32; *tpb = 64; }
+  if (ns <= 64) { *team = 64; *tpb = 64; }
   else { *team = 256; *tpb = 256; }
 }
 

@@ -60,32 +60,36 @@
 #define NTEAM 1
 #endif
 
-// per-cell shared-memory slots (units of SS doubles)
+// per-cell shared-memory slots (units of SS doubles).  The six per-species arrays that only the
+// Jacobian assembly uses (DCP .. JT) alias the stage vectors YT, F, U2..U4, INVD, TMP, which are
+// dead while the Jacobian is formed (it is the first thing a step attempt computes).
 #define OFF_A 0
 #define OFF_Y (OFF_A + NEQ * NEQ)
-#define OFF_YT (OFF_Y + NEQ)
+#define OFF_U1 (OFF_Y + NEQ)
+#define OFF_YT (OFF_U1 + NEQ)
 #define OFF_F (OFF_YT + NEQ)
-#define OFF_U (OFF_F + NEQ)
-#define OFF_INVD (OFF_U + 4 * NEQ)
+#define OFF_U2 (OFF_F + NEQ)
+#define OFF_U3 (OFF_U2 + NEQ)
+#define OFF_U4 (OFF_U3 + NEQ)
+#define OFF_INVD (OFF_U4 + NEQ)
 #define OFF_TMP (OFF_INVD + NEQ)
 #define OFF_C (OFF_TMP + NEQ)
 #define OFF_CP (OFF_C + NS)
 #define OFF_HRT (OFF_CP + NS)
 #define OFF_EX (OFF_HRT + NS)
 #define OFF_IEX (OFF_EX + NS)
-#define OFF_DCP (OFF_IEX + NS)
-#define OFF_OM (OFF_DCP + NS)
-#define OFF_DOMT (OFF_OM + NS)
+#define OFF_OM (OFF_IEX + NS)
+#define OFF_DCP OFF_YT
+#define OFF_DOMT (OFF_DCP + NS)
 #define OFF_BK (OFF_DOMT + NS)
 #define OFF_AL (OFF_BK + NS)
 #define OFF_BE (OFF_AL + NS)
 #define OFF_JT (OFF_BE + NS)
-#define OFF_PIV (OFF_JT + NS)
+#define OFF_PIV (OFF_OM + NS)
 #define OFF_PERM (OFF_PIV + NEQ)
-#define OFF_Q (OFF_PERM + NEQ)
-#define OFF_SEG (OFF_Q + NR)
-#define OFF_RED (OFF_SEG + NSEG)
+#define OFF_RED (OFF_PERM + NEQ)
 #define SLOTS (OFF_RED + 16)
+#define UOFF(i) ((i) == 0 ? OFF_U1 : OFF_U2 + ((i) - 1) * NEQ)
 
 // ------------------------------------------------------------------------------ team plumbing
 
@@ -301,12 +305,9 @@ __device__ __forceinline__ void reaction_loop(const Team& tm, const CellScalars&
     const double m = kind == THIRD ? M : 1.0;
     const double qnet = fwd - rev;
     const double q = m * qnet;
-#if TEAM == 1
-    for (int i = 0; i < nre; ++i) tm.at(OFF_OM, mk_rsp[r][i]) -= mk_rnu[r][i] * q;
-    for (int i = 0; i < npr; ++i) tm.at(OFF_OM, mk_psp[r][i]) += mk_pnu[r][i] * q;
-#else
-    tm.at(OFF_Q, r) = q;  // omega is gathered per species below (no atomics, fixed order)
-#endif
+    // shared-memory reductions without a return value do not stall the lane (TEAM > 1)
+    for (int i = 0; i < nre; ++i) scatter_add<double>(&tm.at(OFF_OM, mk_rsp[r][i]), -mk_rnu[r][i] * q);
+    for (int i = 0; i < npr; ++i) scatter_add<double>(&tm.at(OFF_OM, mk_psp[r][i]), mk_pnu[r][i] * q);
     if (WJ) {
       // d ln Kc / dT = (sum nu'' h/RT - sum nu' h/RT - dnu) / T
       double dlKc = -dnu;
@@ -360,22 +361,6 @@ __device__ __forceinline__ void reaction_loop(const Team& tm, const CellScalars&
     }
   }
   tsync();
-#if TEAM > 1
-  // omega_k = sum_r nu_kr q_r: fixed-length segments of each species' reaction list are summed
-  // by separate lanes, then each species adds its segments in order (deterministic)
-  for (int sg = tm.tl; sg < NSEG; sg += TEAM) {
-    double acc = 0.0;
-    for (int e = mk_gseg_beg[sg]; e < mk_gseg_beg[sg + 1]; ++e) acc += mk_gent_nu[e] * tm.at(OFF_Q, mk_gent_rx[e]);
-    tm.at(OFF_SEG, sg) = acc;
-  }
-  tsync();
-  for (int k = tm.tl; k < NS; k += TEAM) {
-    double acc = 0.0;
-    for (int sg = mk_spseg_beg[k]; sg < mk_spseg_beg[k + 1]; ++sg) acc += tm.at(OFF_SEG, sg);
-    tm.at(OFF_OM, k) = acc;
-  }
-  tsync();
-#endif
 }
 
 // f from omega: f[0] = dT/dt = -T sum_k (h_k/RT) V omega_k / sum_k n_k cp_k/R,
@@ -701,7 +686,7 @@ __device__ void lu_solve(const Team& tm, int ob) {
 // (infinity if anything is non-finite).
 __device__ double ros4_attempt(const Team& tm, double P, double hh, double rtol, double atol,
                               const double* lnA_ext) {
-  const int U1 = OFF_U, U2 = OFF_U + NEQ, U3 = OFF_U + 2 * NEQ, U4 = OFF_U + 3 * NEQ;
+  const int U1 = OFF_U1, U2 = OFF_U2, U3 = OFF_U3, U4 = OFF_U4;
   // stage 1: f0 into U1, M = I/(gamma h) - J
   eval_f_jac(tm, OFF_Y, U1, P, lnA_ext, -1.0, 1.0 / (RGAM * hh));
   lu_factor(tm);
@@ -902,7 +887,7 @@ chem_eval_jacobian_k(long long n_cells, const double* __restrict__ T, const doub
     if (tm.tl == 0) tm.at(OFF_Y, 0) = T[c];
     for (int k = tm.tl; k < NS - 1; k += TEAM) tm.at(OFF_Y, 1 + k) = n[k * ld + c];
     tsync();
-    eval_f_jac(tm, OFF_Y, OFF_F, P[c], lnA_ext, 1.0, 0.0);
+    eval_f_jac(tm, OFF_Y, OFF_U1, P[c], lnA_ext, 1.0, 0.0);  // f goes to U1: F aliases J scratch
     for (int e = tm.tl; e < NEQ * NEQ; e += TEAM) J[(long long)e * ld + c] = tm.at(OFF_A, e);
     tsync();
   }
@@ -1443,7 +1428,7 @@ __device__ __forceinline__ void add_gy(const Team& tm, bool dual, int o1, double
 // J(y) adds sum_i d/dy [w_i^T J(y) u_i] and d/dlnA [w_i^T J(y) u_i] (dual-number VJPs at y along
 // u_i with weights w_i).
 __device__ void adjoint_step(const Team& tm, double P, double h, const double* lnA_ext) {
-  const int U1 = OFF_U, U2 = OFF_U + NEQ, U3 = OFF_U + 2 * NEQ, U4 = OFF_U + 3 * NEQ;
+  const int U1 = OFF_U1, U2 = OFF_U2, U3 = OFF_U3, U4 = OFF_U4;
   const int W1 = AOFF_W, W2 = AOFF_W + NEQ, W3 = AOFF_W + 2 * NEQ, W4 = AOFF_W + 3 * NEQ;
   const int B1 = AOFF_UB, B2 = AOFF_UB + NEQ, B3 = AOFF_UB + 2 * NEQ, B4 = AOFF_UB + 3 * NEQ;
   const double ih = 1.0 / h;
@@ -1540,7 +1525,7 @@ __device__ void adjoint_step(const Team& tm, double P, double h, const double* l
   for (int st = 0; st < 4; ++st) {
     for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(AOFF_V, i) = tm.at(AOFF_W + st * NEQ, i);
     tsync();
-    set_vjp_state<DD>(tm, OFF_Y, OFF_U + st * NEQ);
+    set_vjp_state<DD>(tm, OFF_Y, UOFF(st));
     vjp<DD>(tm, P, lnA_ext);
     add_gy(tm, true, AOFF_YB, 1.0, -1, 0.0, -1, 0.0);
   }
