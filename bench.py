@@ -473,7 +473,9 @@ def main():
 
     # plain one-launch-per-attempt kernel on the same inputs
     plain = None
-    if not args.no_plain and splits == 1:
+    if not args.no_plain:
+        # the plain one-launch-per-attempt driver on the same inputs (split steps run eagerly:
+        # its host polling cannot be captured in a graph)
         po = m.opts(mode=chem.MODE_PLAIN)
         pws = m.workspace(n_cells, po, device=dev)
         pt = []
@@ -482,12 +484,13 @@ def main():
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            one_step(po, pws)
+            for _ in range(splits):
+                one_split(po, pws)
             e1.record(stream)
             e1.synchronize()
             if i:
                 pt.append(e0.elapsed_time(e1) * 1e-3)
-        plain = {"value": n_cells / pt[0], "unit": "cells/s", "ms_per_step": pt[0] * 1e3,
+        plain = {"value": n_cells * splits / pt[0], "unit": "cells/s", "ms_per_step": pt[0] * 1e3,
                  "speedup_of_persistent": pt[0] / sec}
         del pws
 

@@ -485,7 +485,7 @@ __device__ void eval_f_jac(const Team& tm, int oy, int of, double P, const doubl
 
 // In-place LU with partial pivoting of A (N x N): largest |a| in the column, lowest row on
 // ties.  Row swapped with k at step k in OFF_PIV, 1/U_kk in OFF_INVD, and the composed row
-// permutation (row i of P A is row perm[i] of A) in OFF_PERM for the solves.
+// permutation (row i of P A is row perm[i] of A) in OFF_PERM for the transposed solves.
 __device__ void lu_factor(const Team& tm) {
 #if TEAM == 1
   for (int k = 0; k < NEQ; ++k) {
@@ -506,6 +506,8 @@ __device__ void lu_factor(const Team& tm) {
       for (int j = k + 1; j < NEQ; ++j) tm.A(i, j) -= l * tm.A(k, j);
     }
   }
+  for (int i = 0; i < NEQ; ++i) tm.perm(i) = i;
+  for (int k = 0; k < NEQ; ++k) { const int p = tm.piv(k); if (p != k) { const int t = tm.perm(k); tm.perm(k) = tm.perm(p); tm.perm(p) = t; } }
 #else
   for (int k = 0; k < NEQ; ++k) {
     // pivot search: (|a| key desc, row asc)
@@ -541,137 +543,66 @@ __device__ void lu_factor(const Team& tm) {
     if (tm.tl == 0) { tm.piv(k) = p; tm.at(OFF_INVD, k) = inv; }
     for (int i = k + 1 + tm.tl; i < NEQ; i += TEAM) tm.A(i, k) *= inv;
     tsync();
-    // trailing update A[i][j] -= L[i][k] U[k][j], i, j > k, flattened over the m x m block;
-    // four independent elements per iteration so that loads and DFMAs overlap
     const int m = NEQ - k - 1;
     if (m > 0) {
       const int tot = m * m;
       const int qd = TEAM / m, rm = TEAM - qd * m;
-      int i0 = tm.tl / m, j0 = tm.tl - i0 * m;
-      for (int e = tm.tl; e < tot; e += 4 * TEAM) {
-        int ii[4], jj[4];
-        ii[0] = i0; jj[0] = j0;
-#pragma unroll
-        for (int t = 1; t < 4; ++t) {
-          ii[t] = ii[t - 1] + qd;
-          jj[t] = jj[t - 1] + rm;
-          if (jj[t] >= m) { jj[t] -= m; ++ii[t]; }
-        }
-        double a[4], l[4], u[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          if (e + t * TEAM < tot) {
-            a[t] = tm.A(k + 1 + ii[t], k + 1 + jj[t]);
-            l[t] = tm.A(k + 1 + ii[t], k);
-            u[t] = tm.A(k, k + 1 + jj[t]);
-          }
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (e + t * TEAM < tot) tm.A(k + 1 + ii[t], k + 1 + jj[t]) = a[t] - l[t] * u[t];
-        i0 = ii[3] + qd;
-        j0 = jj[3] + rm;
-        if (j0 >= m) { j0 -= m; ++i0; }
+      int i = tm.tl / m, j = tm.tl - (tm.tl / m) * m;
+      for (int e = tm.tl; e < tot; e += TEAM) {
+        tm.A(k + 1 + i, k + 1 + j) -= tm.A(k + 1 + i, k) * tm.A(k, k + 1 + j);
+        i += qd;
+        j += rm;
+        if (j >= m) { j -= m; ++i; }
       }
     }
     tsync();
   }
-#endif
-  // composed permutation for the solves
   if (tm.tl == 0) {
     for (int i = 0; i < NEQ; ++i) tm.perm(i) = i;
-    for (int k = 0; k < NEQ; ++k) {
-      const int p = tm.piv(k);
-      if (p != k) { const int t = tm.perm(k); tm.perm(k) = tm.perm(p); tm.perm(p) = t; }
-    }
+    for (int k = 0; k < NEQ; ++k) { const int p = tm.piv(k); if (p != k) { const int t = tm.perm(k); tm.perm(k) = tm.perm(p); tm.perm(p) = t; } }
   }
   tsync();
+#endif
 }
 
-// Solve (LU) x = P b in place on the vector at slot ob (P from the pivoting).  With TEAM > 1
-// the first warp works: forward and back substitution in 4 x 4 diagonal blocks (each lane
-// solves the small block redundantly, then updates its rows with four FMAs per block).
+// Solve (LU) x = b in place on the vector at slot ob.  With TEAM > 1 only the first warp works.
 __device__ void lu_solve(const Team& tm, int ob) {
 #if TEAM == 1
-  for (int i = 0; i < NEQ; ++i) tm.at(OFF_TMP, i) = tm.at(ob, tm.perm(i));
+  for (int k = 0; k < NEQ; ++k) {
+    const int p = tm.piv(k);
+    if (p != k) { const double t = tm.at(ob, k); tm.at(ob, k) = tm.at(ob, p); tm.at(ob, p) = t; }
+  }
   for (int i = 0; i < NEQ; ++i) {
-    double s = tm.at(OFF_TMP, i);
-    for (int j = 0; j < i; ++j) s -= tm.A(i, j) * tm.at(OFF_TMP, j);
-    tm.at(OFF_TMP, i) = s;
+    double s = tm.at(ob, i);
+    for (int j = 0; j < i; ++j) s -= tm.A(i, j) * tm.at(ob, j);
+    tm.at(ob, i) = s;
   }
   for (int i = NEQ - 1; i >= 0; --i) {
-    double s = tm.at(OFF_TMP, i);
-    for (int j = i + 1; j < NEQ; ++j) s -= tm.A(i, j) * tm.at(OFF_TMP, j);
+    double s = tm.at(ob, i);
+    for (int j = i + 1; j < NEQ; ++j) s -= tm.A(i, j) * tm.at(ob, j);
     tm.at(ob, i) = s * tm.at(OFF_INVD, i);
-    tm.at(OFF_TMP, i) = tm.at(ob, i);
   }
 #else
   if (tm.tl < 32) {
     const int ln = tm.tl;
-    for (int i = ln; i < NEQ; i += 32) tm.at(OFF_TMP, i) = tm.at(ob, tm.perm(i));
+    if (ln == 0)
+      for (int k = 0; k < NEQ; ++k) {
+        const int p = tm.piv(k);
+        if (p != k) { const double t = tm.at(ob, k); tm.at(ob, k) = tm.at(ob, p); tm.at(ob, p) = t; }
+      }
     __syncwarp();
-    // forward: unit lower triangle
-    for (int k0 = 0; k0 < NEQ; k0 += 4) {
-      const int nb = NEQ - k0 < 4 ? NEQ - k0 : 4;
-      double x[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        if (t < nb) {
-          double v = tm.at(OFF_TMP, k0 + t);
-#pragma unroll
-          for (int s2 = 0; s2 < t; ++s2) v -= tm.A(k0 + t, k0 + s2) * x[s2];
-          x[t] = v;
-        } else {
-          x[t] = 0.0;
-        }
-      }
-      __syncwarp();
-      for (int i = k0 + nb + ln; i < NEQ; i += 32) {
-        double v = tm.at(OFF_TMP, i);
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (t < nb) v -= tm.A(i, k0 + t) * x[t];
-        tm.at(OFF_TMP, i) = v;
-      }
-      if (ln < nb) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (t == ln) tm.at(OFF_TMP, k0 + t) = x[t];
-      }
+    for (int k = 0; k < NEQ - 1; ++k) {
+      const double xk = tm.at(ob, k);
+      for (int i = k + 1 + ln; i < NEQ; i += 32) tm.at(ob, i) -= tm.A(i, k) * xk;
       __syncwarp();
     }
-    // back: upper triangle with 1/U_kk
-    for (int k1 = NEQ - 1; k1 >= 0; k1 -= 4) {
-      const int nb = k1 + 1 < 4 ? k1 + 1 : 4;  // rows k1, k1-1, .. k1-nb+1
-      double x[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        if (t < nb) {
-          const int r = k1 - t;
-          double v = tm.at(OFF_TMP, r);
-#pragma unroll
-          for (int s2 = 0; s2 < t; ++s2) v -= tm.A(r, k1 - s2) * x[s2];
-          x[t] = v * tm.at(OFF_INVD, r);
-        } else {
-          x[t] = 0.0;
-        }
-      }
+    for (int k = NEQ - 1; k >= 0; --k) {
+      const double xk = tm.at(ob, k) * tm.at(OFF_INVD, k);
       __syncwarp();
-      for (int i = ln; i <= k1 - nb; i += 32) {
-        double v = tm.at(OFF_TMP, i);
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (t < nb) v -= tm.A(i, k1 - t) * x[t];
-        tm.at(OFF_TMP, i) = v;
-      }
-      if (ln < nb) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (t == ln) tm.at(OFF_TMP, k1 - t) = x[t];
-      }
+      if (ln == (k & 31)) tm.at(ob, k) = xk;
+      for (int i = ln; i < k; i += 32) tm.at(ob, i) -= tm.A(i, k) * xk;
       __syncwarp();
     }
-    for (int i = ln; i < NEQ; i += 32) tm.at(ob, i) = tm.at(OFF_TMP, i);
   }
   tsync();
 #endif
