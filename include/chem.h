@@ -187,6 +187,32 @@ int chem_adjoint(chem_mech_t mech, int64_t n_cells, const double* P, const doubl
                  double* g_lnA, double* gT0, double* gY0, void* workspace, size_t ws_bytes,
                  void* stream);
 
+/* chem_adjoint for callers that cannot allocate device memory.
+ * Some callers cannot call cudaMalloc: code that runs inside a CUDA stream capture (allocation
+ * there is not recorded into the graph), host applications whose device memory is owned by a
+ * fixed pool or by another framework, or embedded solvers that may only touch memory handed to
+ * them.  This entry point needs no workspace and allocates nothing: its scratch (a queue
+ * counter, the recomputed segment states and the per-team partial gradients) lives in a static
+ * device array of CHEM_ADJ_SCRATCH_BYTES (8 MiB) inside the adjoint module; every GPU that loads
+ * that module holds the array until the process exits.  The caller still passes every input and
+ * output, as for chem_adjoint.
+ *   - The first call for a mechanism and kernel configuration compiles and loads the adjoint
+ *     module (as chem_adjoint does) and resolves the array's device address; make that first call
+ *     before any stream capture.
+ *   - The array is shared by all calls on the same module and keeps the last call's contents:
+ *     the entry point zeroes what must start at zero (the queue counter).  Calls whose work
+ *     overlaps on the GPU (other streams, or chem_adjoint_noalloc enqueued twice without an
+ *     ordering between them) race on the array: order them.
+ *   - Fewer teams are launched when the full grid's scratch would not fit; if even one block's
+ *     scratch (interval x Ns + Nr doubles per cell of a block) exceeds the array, it returns
+ *     CHEM_EWS with a message naming the sizes.
+ * (No counterpart in the paper: an addition for callers without an allocator.) */
+#define CHEM_ADJ_SCRATCH_BYTES (8 * 1024 * 1024)
+int chem_adjoint_noalloc(chem_mech_t mech, int64_t n_cells, const double* P, const double* gT,
+                         const double* gY, int64_t ld, const chem_tape* tape,
+                         const chem_int_opts* opts, double* g_lnA, double* gT0, double* gY0,
+                         void* stream);
+
 /* Vector-Jacobian products of f (Eq. e:jac transposed), the adjoint's building block, per cell:
  * gy [Ns x ld] = J(y)^T v and gp [Nr x ld] = (d f / d lnA)^T v, for v [Ns x ld] on the state
  * rows.  T, P, n as in chem_eval_source. */

@@ -24,7 +24,7 @@ EXPORTS = ["chem_mech_load", "chem_mech_compile_only", "chem_mech_free", "chem_m
            "chem_mech_lnA", "chem_eval_source", "chem_eval_jacobian", "chem_integrate_workspace",
            "chem_integrate", "chem_integrate_host", "chem_kernel_config", "chem_autotune",
            "chem_tape_bytes", "chem_integrate_ckpt", "chem_adjoint_workspace", "chem_adjoint",
-           "chem_eval_vjp", "chem_last_error"]
+           "chem_eval_vjp", "chem_adjoint_noalloc", "chem_last_error"]
 STATUS_TAPE_FULL = 5
 
 CACHE_DIR = os.environ.get("CHEM_CACHE_DIR", os.path.join(os.path.dirname(__file__), "_cache"))
@@ -92,6 +92,8 @@ def library(build_if_missing: bool = True):
             lib.chem_adjoint.argtypes = [vp, i64, vp, vp, vp, i64, C.POINTER(TapeStruct),
                                          C.POINTER(IntOpts), vp, vp, vp, vp, C.c_size_t, vp]
             lib.chem_eval_vjp.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i64, vp, vp]
+            lib.chem_adjoint_noalloc.argtypes = [vp, i64, vp, vp, vp, i64, C.POINTER(TapeStruct),
+                                                 C.POINTER(IntOpts), vp, vp, vp, vp]
             lib.chem_autotune.argtypes = [vp, i64, vp, vp, vp, i64, dbl, dbl, dbl, vp,
                                           C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                           C.POINTER(C.c_float)]
@@ -287,6 +289,19 @@ class Mechanism:
         _check(self._lib.chem_adjoint(self._h, Cn, _ptr(P), _ptr(gT), _ptr(gY), Cn,
                                       C.byref(tape.struct), C.byref(o), _ptr(g_lnA), _ptr(gT0),
                                       _ptr(gY0), _ptr(ws), ws.numel(), _stream(stream)))
+        return g_lnA, gT0, gY0
+
+    def adjoint_noalloc(self, P, gT, gY, tape, g_lnA, gT0, gY0, opts=None, stream=None):
+        """chem_adjoint without a workspace (static scratch in the adjoint module); the caller
+        provides the output tensors g_lnA [Nr], gT0 [C], gY0 [Ns, C]."""
+        Cn = P.shape[0]
+        _req(P, "P", shape=(Cn,)); _req(gT, "gT", shape=(Cn,)); _req(gY, "gY", shape=(self.ns, Cn))
+        _req(g_lnA, "g_lnA", shape=(self.nr,)); _req(gT0, "gT0", shape=(Cn,))
+        _req(gY0, "gY0", shape=(self.ns, Cn))
+        o = opts or self.opts()
+        _check(self._lib.chem_adjoint_noalloc(self._h, Cn, _ptr(P), _ptr(gT), _ptr(gY), Cn,
+                                              C.byref(tape.struct), C.byref(o), _ptr(g_lnA),
+                                              _ptr(gT0), _ptr(gY0), _stream(stream)))
         return g_lnA, gT0, gY0
 
     def eval_vjp(self, T, P, n, v, lnA=None, stream=None):

@@ -287,7 +287,7 @@ std::string emit_mechanism(const MechData& m, int team, int tpb, bool adjoint) {
   const int ns = (int)m.sp.size(), nr = (int)m.rx.size();
   std::ostringstream o;
   o << "// generated for mechanism " << m.name << "\n";
-  if (adjoint) o << "#define CHEM_ADJOINT 1\n";
+  if (adjoint) o << "#define CHEM_ADJOINT 1\n#define CHEM_ADJ_SCRATCH_BYTES " << CHEM_ADJ_SCRATCH_BYTES << "\n";
   o << "#define NS " << ns << "\n#define NR " << nr << "\n#define TEAM " << team << "\n#define TPB " << tpb
     << "\n#define MAXP " << kMaxSide << "\n";
   Ros4Coefficients c;
@@ -420,10 +420,12 @@ uint64_t fnv1a(const std::string& s, uint64_t h = 1469598103934665603ULL) {
 const std::vector<std::string> kNvrtcOptions = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo",
                                                 "--ptxas-options=-v", "-DNDEBUG"};
 
-int nvrtc_compile(const std::string& src, const std::string& name, std::string* cubin, std::string* log) {
+int nvrtc_compile(const std::string& src, const std::string& name, std::string* cubin, std::string* log,
+                  const std::vector<std::string>& name_exprs = {}, std::vector<std::string>* lowered = nullptr) {
   nvrtcProgram prog;
   nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), name.c_str(), 0, nullptr, nullptr);
   if (r != NVRTC_SUCCESS) return fail(CHEM_ENVRTC, "nvrtcCreateProgram: %s", nvrtcGetErrorString(r));
+  for (auto& e : name_exprs) nvrtcAddNameExpression(prog, e.c_str());
   std::vector<const char*> opts;
   for (auto& s : kNvrtcOptions) opts.push_back(s.c_str());
   r = nvrtcCompileProgram(prog, (int)opts.size(), opts.data());
@@ -437,6 +439,17 @@ int nvrtc_compile(const std::string& src, const std::string& name, std::string* 
     return fail(CHEM_ENVRTC, "NVRTC compile of %s failed: %s\n%s", name.c_str(), nvrtcGetErrorString(r),
                 lg.substr(0, 1500).c_str());
   }
+  if (lowered) {
+    lowered->clear();
+    for (auto& e : name_exprs) {
+      const char* low = nullptr;
+      if (nvrtcGetLoweredName(prog, e.c_str(), &low) != NVRTC_SUCCESS || !low) {
+        nvrtcDestroyProgram(&prog);
+        return fail(CHEM_ENVRTC, "no lowered name for %s", e.c_str());
+      }
+      lowered->push_back(low);
+    }
+  }
   size_t n = 0;
   nvrtcGetCUBINSize(prog, &n);
   cubin->resize(n);
@@ -444,6 +457,12 @@ int nvrtc_compile(const std::string& src, const std::string& name, std::string* 
   nvrtcDestroyProgram(&prog);
   return 0;
 }
+
+// The adjoint module's static scratch array (used by chem_adjoint_noalloc only): the name
+// expression that keeps it in the module, and its lowered (internal-linkage) symbol name, which
+// is checked against NVRTC's whenever the module is compiled.
+const char* const kAdjScratchExpr = "&chem_adj_scratch";
+const char* const kAdjScratchSym = "chem_adj_scratch";
 
 // cubin for (mechanism, team, block): from cache_dir if present, else compiled (and stored)
 int build_cubin(const MechData& m, int team, int tpb, bool adjoint, const char* cache_dir, bool verbose,
@@ -469,7 +488,11 @@ int build_cubin(const MechData& m, int team, int tpb, bool adjoint, const char* 
     }
   }
   std::string lg;
-  int rc = nvrtc_compile(src, m.name + ".cu", cubin, &lg);
+  std::vector<std::string> exprs, lowered;
+  if (adjoint) exprs.push_back(kAdjScratchExpr);
+  int rc = nvrtc_compile(src, m.name + ".cu", cubin, &lg, exprs, &lowered);
+  if (!rc && adjoint && lowered[0] != kAdjScratchSym)
+    return fail(CHEM_ENVRTC, "unexpected lowered name %s for the adjoint scratch", lowered[0].c_str());
   if (log) *log = lg;
   if (verbose && !lg.empty()) fprintf(stderr, "[chem] %s team=%d block=%d\n%s\n", m.name.c_str(), team, tpb, lg.c_str());
   if (rc) return rc;
@@ -493,6 +516,8 @@ struct Module {
   int smem = 0;          // dynamic shared memory per block
   int adj_smem = 0;      // ... of the adjoint / VJP kernels (0: not available for this config)
   int adj_occ = 0;
+  CUdeviceptr adj_scratch = 0;   // device address of the adjoint module's static scratch array
+  size_t adj_scratch_bytes = 0;
   int occ = 0;           // resident blocks per SM for f_int
   int regs = 0;
 };
@@ -1035,6 +1060,72 @@ int chem_adjoint(chem_mech_t m, int64_t n_cells, const double* P, const double* 
                   (void*)&tck, &interval, &seg, &part, &q};
   const unsigned grid = (unsigned)(teams / teams_per_block(mod));
   CU_TRY(drv::cuLaunchKernel(mod->f_adj, grid, 1, 1, mod->tpb, 1, 1, mod->adj_smem, s, args, nullptr));
+  void* rargs[] = {&nparts, &part, &g_lnA};
+  CU_TRY(drv::cuLaunchKernel(mod->f_adjred, (unsigned)((nr + 127) / 128), 1, 1, 128, 1, 1, 0, s, rargs, nullptr));
+  return 0;
+}
+
+int chem_adjoint_noalloc(chem_mech_t m, int64_t n_cells, const double* P, const double* gT, const double* gY,
+                         int64_t ld, const chem_tape* tape, const chem_int_opts* o, double* g_lnA, double* gT0,
+                         double* gY0, void* stream) {
+  if (!m) return fail(CHEM_EARG, "NULL mechanism");
+  if (int rc = check_cells(n_cells, ld)) return rc;
+  if (!P || !gT || !gY || !g_lnA || !gT0 || !gY0) return fail(CHEM_EARG, "NULL array");
+  if (int rc = check_tape(m, n_cells, tape)) return rc;
+  if (int rc = make_current(m)) return rc;
+  Module* mod;
+  if (int rc = adjoint_module(m, o, &mod)) return rc;
+  {
+    // set-up, once per loaded adjoint module (one per device context, made current above): the
+    // device address of the module's static scratch array
+    std::lock_guard<std::mutex> lk(m->mu);
+    if (!mod->adj_scratch) {
+      CUdeviceptr p = 0;
+      size_t bytes = 0;
+      CU_TRY(drv::cuModuleGetGlobal(&p, &bytes, mod->mod, kAdjScratchSym));
+      if (bytes < (size_t)CHEM_ADJ_SCRATCH_BYTES)
+        return fail(CHEM_ECUDA, "static adjoint scratch is %zu bytes, expected %d", bytes, (int)CHEM_ADJ_SCRATCH_BYTES);
+      mod->adj_scratch_bytes = bytes;
+      mod->adj_scratch = p;
+    }
+  }
+  const int ns = (int)m->data.sp.size(), nr = (int)m->data.rx.size();
+  CUstream s = (CUstream)stream;
+  if (n_cells == 0) {
+    CU_TRY(drv::cuMemsetD32Async((CUdeviceptr)g_lnA, 0, 2 * (size_t)nr, s));
+    return 0;
+  }
+  // scratch: [queue counter: 256 B][segment states: teams x interval x Ns][partials: teams x Nr]
+  const size_t per_team = sizeof(double) * ((size_t)tape->interval * ns + nr);
+  const size_t room = (size_t)CHEM_ADJ_SCRATCH_BYTES - 512;
+  const int64_t tpb = teams_per_block(mod);
+  const int64_t fit_blocks = (int64_t)(room / (per_team * (size_t)tpb));
+  if (fit_blocks < 1)
+    return fail(CHEM_EWS,
+                "chem_adjoint_noalloc: one block of %lld cells needs %zu bytes of scratch (interval %d x %d species + "
+                "%d reactions per cell); the static scratch holds %d bytes -- lower the checkpoint interval or "
+                "use chem_adjoint with a workspace",
+                (long long)tpb, per_team * (size_t)tpb, tape->interval, ns, nr, (int)CHEM_ADJ_SCRATCH_BYTES);
+  int64_t teams = adjoint_teams(m, mod, n_cells);
+  teams = std::min<int64_t>(teams, fit_blocks * tpb);
+  const CUdeviceptr base = mod->adj_scratch;
+  CUdeviceptr q = base;
+  double* seg = (double*)(base + 256);
+  double* part = (double*)(base + 256 + align256(sizeof(double) * teams * (size_t)tape->interval * ns));
+  const TapeLayout L = tape_layout(ns, n_cells, tape->capacity, tape->interval);
+  char* tb = (char*)tape->mem;
+  const int* tnacc = (const int*)(tb + L.nacc);
+  const double* th = (const double*)(tb + L.h);
+  const double* tck = (const double*)(tb + L.ck);
+  const double* lnA = o ? o->lnA : nullptr;
+  int interval = tape->interval;
+  long long nc = n_cells, l = ld, nparts = teams;
+  // the scratch keeps the previous call's contents: the queue counter must start at zero; the
+  // segment states and the partial rows are written before they are read
+  CU_TRY(drv::cuMemsetD32Async(q, 0, 2, s));
+  void* args[] = {&nc, (void*)&P, (void*)&gT, (void*)&gY, &l, &gT0, &gY0, (void*)&lnA, (void*)&tnacc, (void*)&th,
+                  (void*)&tck, &interval, &seg, &part, &q};
+  CU_TRY(drv::cuLaunchKernel(mod->f_adj, (unsigned)(teams / tpb), 1, 1, mod->tpb, 1, 1, mod->adj_smem, s, args, nullptr));
   void* rargs[] = {&nparts, &part, &g_lnA};
   CU_TRY(drv::cuLaunchKernel(mod->f_adjred, (unsigned)((nr + 127) / 128), 1, 1, 128, 1, 1, 0, s, rargs, nullptr));
   return 0;

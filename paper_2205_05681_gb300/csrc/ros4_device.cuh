@@ -1464,6 +1464,11 @@ __device__ void adjoint_step(const Team& tm, double P, double h, const double* l
   tsync();
 }
 
+// Scratch of chem_adjoint_noalloc (the adjoint for callers that cannot allocate device memory):
+// a fixed array in this module, CHEM_ADJ_SCRATCH_BYTES long, shared by every call on this
+// module; the host resolves its device address once per loaded module.
+static __device__ __align__(256) double chem_adj_scratch[CHEM_ADJ_SCRATCH_BYTES / 8];
+
 __device__ __forceinline__ long long team_global_id() {
   return (long long)blockIdx.x * NTEAM + (TEAM == 32 ? (threadIdx.x >> 5) : 0);
 }
