@@ -184,7 +184,7 @@ def cpu_oracle_rate(path, wl, budget_s=15.0, max_cells=4096):
     t0 = time.perf_counter()
     run(idx, y)
     per = (time.perf_counter() - t0) / len(idx)
-    ns = int(min(max_cells, max(len(idx), budget_s / max(per, 1e-9))))
+    ns = int(min(max_cells, n_cells, max(len(idx), budget_s / max(per, 1e-9))))
     idx = np.linspace(0, n_cells - 1, ns).astype(int)
     y = sample_states(idx)
     t0 = time.perf_counter()
@@ -222,12 +222,17 @@ def relax_products(m, st, T0, P, Y0, torch, np, n_templates=1024, t_relax=1e-3):
             "front_cells": int(front.sum()), "product_cells": int(len(idx))}
 
 
-def adjoint_leg(chem, synth, torch, np, dev, path53):
-    """Checkpointed forward + discrete adjoint on the 53-species ignition workload (16,384 cells,
-    1e-4 s): loss = sum (T - T_target)^2 with T_target from a seeded ln A perturbation + noise;
-    times the taped forward, the plain forward and the reverse sweep (CUDA events)."""
-    mech_name, n, recipe, seed, dt, _ = synth.WORKLOADS["ch4_53_adjoint"]
-    st = synth.make_states(synth.mechanism(mech_name), n, recipe, seed)
+def adjoint_leg(chem, synth, torch, np, dev, path53, wl="ch4_53_adjoint", cells=0, cap=4096,
+                interval=16):
+    """Checkpointed forward + discrete adjoint on an ignition workload (default: 53 species,
+    16,384 cells, 1e-4 s): loss = sum (T - T_target)^2 with T_target from a seeded ln A
+    perturbation + noise; times the taped forward, the plain forward and the reverse sweep (CUDA
+    events)."""
+    mech_name, n, recipe, seed, dt, _ = synth.WORKLOADS[wl]
+    if cells:
+        n = min(n, cells)
+    st = synth.make_states(synth.mechanism(mech_name), synth.WORKLOADS[wl][1], recipe, seed)
+    st = synth.States(st.T[:n], st.P[:n], st.Y[:n])
     m = chem.Mechanism(synth.mechanism_file(mech_name, MECH_DIR))
     T0 = torch.tensor(st.T, device=dev)
     P = torch.tensor(st.P, device=dev)
@@ -238,7 +243,6 @@ def adjoint_leg(chem, synth, torch, np, dev, path53):
     Tt, Yt = T0.clone(), Y0.clone()
     m.integrate(Tt, P, Yt, dt, opts=m.opts(lnA=lnA_t))
     T_target = Tt + torch.tensor(rng.normal(0.0, 1.0, n), device=dev)
-    interval, cap = 16, 4096
     tape = m.make_tape(n, cap, interval, device=dev)
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     status = torch.empty(n, dtype=torch.int32, device=dev)
@@ -267,7 +271,7 @@ def adjoint_leg(chem, synth, torch, np, dev, path53):
         e1.record()
         e1.synchronize()
         t_plain = e0.elapsed_time(e1)
-        res = {"workload": "ch4_53_adjoint", "cells": n, "dt_s": dt, "interval": interval,
+        res = {"workload": wl, "cells": n, "dt_s": dt, "interval": interval, "capacity": cap,
                "fwd_ckpt_ms": t_fwd, "fwd_ms": t_plain, "adjoint_ms": t_adj,
                "adjoint_over_fwd": t_adj / t_plain, "tape_bytes": int(tape.buf.numel()),
                "accepted_mean": float(tape.n_accepted().float().mean().item()),
@@ -347,6 +351,8 @@ def main():
                     help="use only the first CELLS cells of the workload (small profiling runs)")
     ap.add_argument("--autotune", action="store_true", help="pick (team, block) on a sample first")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward leg")
+    ap.add_argument("--tape-capacity", type=int, default=4096, help="adjoint workloads: steps/cell")
+    ap.add_argument("--interval", type=int, default=16, help="adjoint workloads: checkpoint interval")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -361,6 +367,16 @@ def main():
     torch.cuda.set_device(dev)
 
     wl = args.workload
+    if wl.endswith("_adjoint"):
+        res = adjoint_leg(chem, synth, torch, np, dev, None, wl=wl, cells=args.cells,
+                          cap=args.tape_capacity, interval=args.interval)
+        if rank == 0:
+            line = {"metric": "adjoint/forward time (discrete adjoint, ROS4, FP64)",
+                    "value": res["adjoint_over_fwd"], "unit": "x", "n_gpus": world,
+                    "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+                    "config": {"workload": wl}, "adjoint": res}
+            print(json.dumps(line), flush=True)
+        return 0
     mech_name, n_cells, recipe, seed, dt, splits = synth.WORKLOADS[wl]
     path = synth.mechanism_file(mech_name, MECH_DIR + ("" if world == 1 else "_r%d" % rank))
     t0 = time.perf_counter()

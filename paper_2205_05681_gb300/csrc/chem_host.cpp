@@ -547,7 +547,7 @@ namespace {
 int slots_for(const MechData& m) {
   const int ns = (int)m.sp.size(), nr = (int)m.rx.size();
   (void)nr;
-  return ns * ns + 17 * ns + 16;
+  return ns * ns + 17 * ns + 24;
 }
 
 // default kernel configuration by mechanism size (the autotuner's usual pick on GB300):
@@ -603,8 +603,11 @@ int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = fal
   CU_TRY(drv::cuMemcpyDtoH(&dev_slots, slots_ptr, sizeof(int)));
   if (dev_slots != slots_for(m->data))
     return fail(CHEM_ECUDA, "shared-memory layout mismatch (%d vs %d)", dev_slots, slots_for(m->data));
-  for (CUfunction f : {mod->f_source, mod->f_jac, mod->f_int, mod->f_pinit, mod->f_patt})
+  for (CUfunction f : {mod->f_source, mod->f_jac, mod->f_int, mod->f_pinit, mod->f_patt}) {
     CU_TRY(drv::cuFuncSetAttribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem));
+    // all of L1 as shared memory: occupancy is bounded by the cells' shared-memory footprint
+    CU_TRY(drv::cuFuncSetAttribute(f, CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, 100));
+  }
   CU_TRY(drv::cuOccupancyMaxActiveBlocksPerMultiprocessor(&mod->occ, mod->f_int, tpb, smem));
   if (adjoint && team > 1) {
     CUdeviceptr ap;
@@ -618,6 +621,7 @@ int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = fal
       CU_TRY(drv::cuModuleGetFunction(&mod->f_adjred, mod->mod, "chem_adjoint_reduce_k"));
       CU_TRY(drv::cuModuleGetFunction(&mod->f_vjp, mod->mod, "chem_eval_vjp_k"));
       CU_TRY(drv::cuFuncSetAttribute(mod->f_adj, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, asmem));
+      CU_TRY(drv::cuFuncSetAttribute(mod->f_adj, CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, 100));
       CU_TRY(drv::cuFuncSetAttribute(mod->f_vjp, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, asmem));
       CU_TRY(drv::cuOccupancyMaxActiveBlocksPerMultiprocessor(&mod->adj_occ, mod->f_adj, tpb, asmem));
       if (mod->adj_occ >= 1) mod->adj_smem = asmem;

@@ -36,7 +36,10 @@
 #define TROE 3
 
 #define R_U 8314.462618
+#define INV_R_U (1.0 / 8314.462618)
 #define P_ATM 101325.0
+#define R_OVER_PATM (8314.462618 / 101325.0)
+#define PATM_OVER_R (101325.0 / 8314.462618)
 #define LN10 2.302585092994046
 
 #define ST_OK 0
@@ -88,7 +91,7 @@
 #define OFF_PIV (OFF_OM + NS)
 #define OFF_PERM (OFF_PIV + NEQ)
 #define OFF_RED (OFF_PERM + NEQ)
-#define SLOTS (OFF_RED + 16)
+#define SLOTS (OFF_RED + 24)
 #define UOFF(i) ((i) == 0 ? OFF_U1 : OFF_U2 + ((i) - 1) * NEQ)
 
 // ------------------------------------------------------------------------------ team plumbing
@@ -163,12 +166,44 @@ struct CellScalars {
   double T, invT, lnT, V, cpm, dcpm;  // cpm = sum n_k cp_k / R, dcpm = sum n_k dcp_k/dT / R
 };
 
+// mass closure: n_bath = (1 - sum_k W_k n_k) / W_bath; n_tot = sum of all moles; V = n_tot R T/P
+__device__ __forceinline__ void closure_scalars(double T, double P, double wsum, double nsum, double* out) {
+  const double nb = (1.0 - wsum) * mk_invW[BATH];
+  const double V = (nsum + nb) * R_U * T / P;
+  out[0] = 1.0 / T;
+  out[1] = log(T);
+  out[2] = nb;
+  out[3] = V;
+  out[4] = 1.0 / V;
+}
+
 template <bool WJ>
 __device__ __forceinline__ void thermo_conc(const Team& tm, int oy, double P, CellScalars& cs) {
   const double T = tm.at(oy, 0);
-  const double invT = 1.0 / T;
-  const double lnT = log(T);
-  // mass closure: n_bath = (1 - sum_k W_k n_k) / W_bath; n_tot = sum of all moles
+  double sc[5];
+#if TEAM > 32
+  // one lane computes the cell's scalars (divisions, log) and shares them: every extra warp
+  // repeating them would pay full warp-level FP64 pipe time
+  if (tm.tl < 32) {
+    double wsum = 0.0, nsum = 0.0;
+    for (int k = tm.tl; k < NS - 1; k += 32) {
+      const double n = tm.at(oy, 1 + k);
+      wsum += mk_W[k] * n;
+      nsum += n;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+      nsum += __shfl_xor_sync(0xffffffffu, nsum, o);
+    }
+    if (tm.tl == 0) {
+      closure_scalars(T, P, wsum, nsum, sc);
+      for (int i = 0; i < 5; ++i) tm.base[OFF_RED + 16 + i] = sc[i];
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < 5; ++i) sc[i] = tm.base[OFF_RED + 16 + i];
+#else
   double wsum = 0.0, nsum = 0.0;
   for (int k = tm.tl; k < NS - 1; k += TEAM) {
     const double n = tm.at(oy, 1 + k);
@@ -177,10 +212,9 @@ __device__ __forceinline__ void thermo_conc(const Team& tm, int oy, double P, Ce
   }
   wsum = team_sum(tm, wsum);
   nsum = team_sum(tm, nsum);
-  const double nb = (1.0 - wsum) * mk_invW[BATH];
-  const double ntot = nsum + nb;
-  const double V = ntot * R_U * T / P;
-  const double invV = 1.0 / V;
+  closure_scalars(T, P, wsum, nsum, sc);
+#endif
+  const double invT = sc[0], lnT = sc[1], nb = sc[2], V = sc[3], invV = sc[4];
   double cpm = 0.0, dcpm = 0.0;
   for (int k = tm.tl; k < NS; k += TEAM) {
     const double n = k < NS - 1 ? tm.at(oy, 1 + k) : nb;
@@ -227,9 +261,9 @@ template <bool WJ>
 __device__ __forceinline__ void reaction_loop(const Team& tm, const CellScalars& cs, double P,
                                               const double* __restrict__ lnA_ext) {
   const double T = cs.T, invT = cs.invT, lnT = cs.lnT;
-  const double Ctot = P * invT / R_U;       // sum_k C_k = P / (R T)
-  const double rtp = R_U * T / P_ATM;       // (P_atm / R T)^-1
-  const double irtp = 1.0 / rtp;
+  const double Ctot = P * invT * INV_R_U;    // sum_k C_k = P / (R T)
+  const double rtp = R_OVER_PATM * T;       // (P_atm / R T)^-1
+  const double irtp = PATM_OVER_R * invT;
   for (int r = tm.tl; r < NR; r += TEAM) {
     const int kind = mk_kind[r];
     const double lA = lnA_ext ? lnA_ext[r] : mk_lnA[r];
@@ -408,8 +442,8 @@ __device__ void eval_f_jac(const Team& tm, int oy, int of, double P, const doubl
   reaction_loop<true>(tm, cs, P, lnA_ext);
   const double fT = source_from_omega(tm, cs, of);
   const double T = cs.T, V = cs.V, invT = cs.invT;
-  const double RTP = R_U * T / P;
-  const double Ctot = P * invT / R_U;
+  const double Ctot = P * invT * INV_R_U;
+  const double RTP = 1.0 / Ctot;  // R T / P
   // per species row k (B_k = default-efficiency third-body part, added to every column):
   //   D_k = omega_k - sum_m (d omega_k/dC_m) C_m,
   //   d f_k/d n_j = d omega_k/dC_j - w_j d omega_k/dC_bath + (RT/P)(1 - w_j) D_k
@@ -417,8 +451,17 @@ __device__ void eval_f_jac(const Team& tm, int oy, int of, double P, const doubl
   //   d f_k / dT = V (D_k / T + d omega_k/dT).
   for (int k = tm.tl; k < NS; k += TEAM) {
     const int row = smap(k);
-    double dot = 0.0;
-    for (int j = 0; j < NS; ++j) dot += tm.A(row, smap(j)) * tm.at(OFF_C, j);
+    // four partial sums: independent FMA chains instead of one NS-long dependent chain
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+    int j = 0;
+    for (; j + 3 < NS; j += 4) {
+      d0 += tm.A(row, smap(j)) * tm.at(OFF_C, j);
+      d1 += tm.A(row, smap(j + 1)) * tm.at(OFF_C, j + 1);
+      d2 += tm.A(row, smap(j + 2)) * tm.at(OFF_C, j + 2);
+      d3 += tm.A(row, smap(j + 3)) * tm.at(OFF_C, j + 3);
+    }
+    for (; j < NS; ++j) d0 += tm.A(row, smap(j)) * tm.at(OFF_C, j);
+    const double dot = (d0 + d1) + (d2 + d3);
     const double Bk = tm.at(OFF_BK, k);
     const double D = tm.at(OFF_OM, k) - dot - Bk * Ctot;
     tm.at(OFF_AL, k) = tm.A(row, 0) + Bk + RTP * D;
@@ -458,8 +501,16 @@ __device__ void eval_f_jac(const Team& tm, int oy, int of, double P, const doubl
   const double hb = tm.at(OFF_HRT, BATH), alb = tm.at(OFF_AL, BATH), beb = tm.at(OFF_BE, BATH);
   const double icpm = 1.0 / cs.cpm;
   for (int l = tm.tl; l < NEQ; l += TEAM) {
-    double s = 0.0;
-    for (int i = 1; i < NEQ; ++i) s += tm.at(OFF_HRT, i - 1) * tm.A(i, l);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = 1;
+    for (; i + 3 < NEQ; i += 4) {
+      s0 += tm.at(OFF_HRT, i - 1) * tm.A(i, l);
+      s1 += tm.at(OFF_HRT, i) * tm.A(i + 1, l);
+      s2 += tm.at(OFF_HRT, i + 1) * tm.A(i + 2, l);
+      s3 += tm.at(OFF_HRT, i + 2) * tm.A(i + 3, l);
+    }
+    for (; i < NEQ; ++i) s0 += tm.at(OFF_HRT, i - 1) * tm.A(i, l);
+    double s = (s0 + s1) + (s2 + s3);
     if (l > 0) s -= tm.at(OFF_HRT, l - 1) * shift;  // remove the diagonal shift of M
     s *= sgn;  // the rows above carry the sign
     double val;
@@ -539,9 +590,13 @@ __device__ void lu_factor(const Team& tm) {
     if (p != k)
       for (int j = tm.tl; j < NEQ; j += TEAM) { const double t = tm.A(k, j); tm.A(k, j) = tm.A(p, j); tm.A(p, j) = t; }
     tsync();
-    const double inv = 1.0 / tm.A(k, k);
-    if (tm.tl == 0) { tm.piv(k) = p; tm.at(OFF_INVD, k) = inv; }
-    for (int i = k + 1 + tm.tl; i < NEQ; i += TEAM) tm.A(i, k) *= inv;
+    // 1/pivot and the column scale by the first warp only: a warp-level FP64 instruction costs the
+    // same pipe time whatever its lane count, so the other warps must not repeat the division
+    if (tm.tl < 32) {
+      const double inv = 1.0 / tm.A(k, k);
+      if (tm.tl == 0) { tm.piv(k) = p; tm.at(OFF_INVD, k) = inv; }
+      for (int i = k + 1 + tm.tl; i < NEQ; i += 32) tm.A(i, k) *= inv;
+    }
     tsync();
     const int m = NEQ - k - 1;
     if (m > 0) {
@@ -827,7 +882,11 @@ chem_eval_jacobian_k(long long n_cells, const double* __restrict__ T, const doub
 // Persistent driver: each team pulls cells from the queue counter and integrates them to dt.
 // With TEAM == 1 each thread refills independently (per-lane refill of retired cells); the
 // loop body is one step attempt so that lanes on different cells still execute it together.
-extern "C" __global__ void __launch_bounds__(TPB)
+// Registers capped so that the cells that fit in shared memory can all be resident: seven
+// 64-lane teams (53 species) or two 256-lane teams (111 species) per SM (GB300, 53 species:
+// 24.2K vs 22.7K cells/s with the cap)
+#define MIN_BLOCKS (TEAM == 64 ? 7 : (TEAM >= 128 ? 2 : 1))
+extern "C" __global__ void __launch_bounds__(TPB, MIN_BLOCKS)
 chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __restrict__ P,
                  double* __restrict__ Y, long long ld, double dt, double rtol, double atol,
                  double* __restrict__ h_io, int* __restrict__ status_out,
