@@ -416,17 +416,19 @@ void lu_solve(int n, const S* LU, const int* piv, S* b) {
 // (The paper prints sum_{j<=i} and c = gamma I - Gamma^-1; the diagonal belongs to the left-hand
 //  side, so the sums run over j < i and C = diag(1/gamma) - Gamma^-1.)
 struct Tableau {
-  int s = 4;
+  int s = 4;       // stages
+  int order = 4;   // order of the main solution (the controller uses err^(-1/order))
   double gamma;
-  double a[4][4];
-  double c[4][4];
-  double m[4];
-  double e[4];
+  double a[6][6];
+  double c[6][6];
+  double m[6];
+  double e[6];
 };
 
 static Tableau ros4_hw() {
   Tableau t{};
   t.s = 4;
+  t.order = 4;
   t.gamma = 0.57282;
   t.a[1][0] = 2.0;
   t.a[2][0] = 1.867943637803922;
@@ -448,6 +450,99 @@ static Tableau ros4_hw() {
   t.e[2] = -0.1082196201495311;
   t.e[3] = -1.093502252409163;
   return t;
+}
+
+// Sandu, Verwer, Blom, Spee, Carmichael & Potra (1997), "Benchmarking stiff ODE solvers for
+// atmospheric chemistry problems II: Rosenbrock solvers": ROS3, 3 stages, order 3(2), L-stable.
+static Tableau ros3_sandu() {
+  Tableau t{};
+  t.s = 3;
+  t.order = 3;
+  t.gamma = 0.43586652150845899941601945119356;
+  t.a[1][0] = 1.0;
+  t.a[2][0] = 1.0;
+  t.c[1][0] = -1.0156171083877702091975600115545;
+  t.c[2][0] = 4.0759956452537699824805835358067;
+  t.c[2][1] = 9.2076794298330791242156818474003;
+  t.m[0] = 1.0;
+  t.m[1] = 6.1697947043828245592553615689730;
+  t.m[2] = -0.42772256543218573326238373806514;
+  t.e[0] = 0.5;
+  t.e[1] = -2.9079558716805469821718236208017;
+  t.e[2] = 0.22354069897811569627360909276199;
+  return t;
+}
+
+// Sandu et al. (1997): RODAS3, 4 stages, order 3(2), stiffly accurate.
+static Tableau rodas3_sandu() {
+  Tableau t{};
+  t.s = 4;
+  t.order = 3;
+  t.gamma = 0.5;
+  t.a[2][0] = 2.0;
+  t.a[3][0] = 2.0;
+  t.a[3][2] = 1.0;
+  t.c[1][0] = 4.0;
+  t.c[2][0] = 1.0;
+  t.c[2][1] = -1.0;
+  t.c[3][0] = 1.0;
+  t.c[3][1] = -1.0;
+  t.c[3][2] = -8.0 / 3.0;
+  t.m[0] = 2.0;
+  t.m[2] = 1.0;
+  t.m[3] = 1.0;
+  t.e[3] = 1.0;
+  return t;
+}
+
+// Hairer & Wanner, Solving ODEs II, Sec. VI.4: RODAS4, 6 stages, order 4(3), stiffly accurate.
+static Tableau rodas4_hw() {
+  Tableau t{};
+  t.s = 6;
+  t.order = 4;
+  t.gamma = 0.25;
+  t.a[1][0] = 1.544;
+  t.a[2][0] = 0.9466785280815826;
+  t.a[2][1] = 0.2557011698983284;
+  t.a[3][0] = 3.314825187068521;
+  t.a[3][1] = 2.896124015972201;
+  t.a[3][2] = 0.9986419139977817;
+  t.a[4][0] = 1.221224509226641;
+  t.a[4][1] = 6.019134481288629;
+  t.a[4][2] = 12.53708332932087;
+  t.a[4][3] = -0.6878860361058950;
+  for (int j = 0; j < 4; ++j) t.a[5][j] = t.a[4][j];
+  t.a[5][4] = 1.0;
+  t.c[1][0] = -5.6688;
+  t.c[2][0] = -2.430093356833875;
+  t.c[2][1] = -0.2063599157091915;
+  t.c[3][0] = -0.1073529058151375;
+  t.c[3][1] = -9.594562251023355;
+  t.c[3][2] = -20.47028614809616;
+  t.c[4][0] = 7.496443313967647;
+  t.c[4][1] = -10.24680431464352;
+  t.c[4][2] = -33.99990352819905;
+  t.c[4][3] = 11.70890893206160;
+  t.c[5][0] = 8.083246795921522;
+  t.c[5][1] = -7.981132988064893;
+  t.c[5][2] = -31.52159432874371;
+  t.c[5][3] = 16.31930543123136;
+  t.c[5][4] = -6.058818238834054;
+  for (int j = 0; j < 4; ++j) t.m[j] = t.a[4][j];
+  t.m[4] = 1.0;
+  t.m[5] = 1.0;
+  t.e[5] = 1.0;
+  return t;
+}
+
+// Rosenbrock methods of Table T:solvers by id: 0 ROS4 (default), 1 ROS3, 2 RODAS3, 3 RODAS4
+static Tableau tableau_by_id(int id) {
+  switch (id) {
+    case 1: return ros3_sandu();
+    case 2: return rodas3_sandu();
+    case 3: return rodas4_hw();
+    default: return ros4_hw();
+  }
 }
 
 // An ODE system y' = F(y) with Jacobian; Sys provides rhs() and jac() for scalar S.
@@ -570,7 +665,7 @@ IntResult integrate_one(const Sys& sys, const Tableau& tb, double* y, double dt,
     double err = err_norm(N, y, ynew.data(), e.data(), o.rtol, o.atol);
     bool finite = std::isfinite(err);
     for (int i = 0; i < N && finite; ++i) finite = std::isfinite(ynew[i]);
-    double fac = finite ? std::min(6.0, std::max(0.2, 0.9 * std::pow(std::max(err, 1e-10), -0.25))) : 0.2;
+    double fac = finite ? std::min(6.0, std::max(0.2, 0.9 * std::pow(std::max(err, 1e-10), -1.0 / tb.order))) : 0.2;
     if (finite && err <= 1.0) {
       for (int i = 0; i < N; ++i) y[i] = ynew[i];
       res.accepted++;
@@ -713,35 +808,38 @@ int orc_rates(void* h, const double* y, double P, const double* lnA, double* kf,
   return 0;
 }
 
-// tableau: gamma, a[4][4], c[4][4], m[4], e[4]  (41 doubles)
-int orc_tableau(double* out) {
-  Tableau t = ros4_hw();
-  out[0] = t.gamma;
-  for (int i = 0; i < 4; ++i) for (int j = 0; j < 4; ++j) { out[1 + i * 4 + j] = t.a[i][j]; out[17 + i * 4 + j] = t.c[i][j]; }
-  for (int i = 0; i < 4; ++i) { out[33 + i] = t.m[i]; out[37 + i] = t.e[i]; }
+// tableau `id`: s, order, gamma, a[6][6], c[6][6], m[6], e[6]  (87 doubles)
+int orc_tableau(int id, double* out) {
+  Tableau t = tableau_by_id(id);
+  out[0] = t.s;
+  out[1] = t.order;
+  out[2] = t.gamma;
+  for (int i = 0; i < 6; ++i) for (int j = 0; j < 6; ++j) { out[3 + i * 6 + j] = t.a[i][j]; out[39 + i * 6 + j] = t.c[i][j]; }
+  for (int i = 0; i < 6; ++i) { out[75 + i] = t.m[i]; out[81 + i] = t.e[i]; }
   return 0;
 }
 
 // one ROS4 step on y' = A y (A n x n row-major)
-int orc_step_linear(int n, const double* A, const double* y, double h, double* ynew, double* err) {
+int orc_step_linear(int n, const double* A, const double* y, double h, double* ynew, double* err, int tab) {
   LinSys<double> sys{n, A};
-  ros4_step(sys, ros4_hw(), y, h, ynew, err);
+  ros4_step(sys, tableau_by_id(tab), y, h, ynew, err);
   return 0;
 }
 
-int orc_integrate_linear(int n, const double* A, double* y, double dt, double rtol, double atol, int* attempts) {
+int orc_integrate_linear(int n, const double* A, double* y, double dt, double rtol, double atol, int* attempts,
+                         int tab) {
   LinSys<double> sys{n, A};
   IntOpts o; o.rtol = rtol; o.atol = atol;
-  IntResult r = integrate_one(sys, ros4_hw(), y, dt, 0.0, o, nullptr);
+  IntResult r = integrate_one(sys, tableau_by_id(tab), y, dt, 0.0, o, nullptr);
   *attempts = r.attempts;
   return r.status;
 }
 
 // one ROS4 step of the chemistry of one cell
-int orc_step(void* h, const double* y, double P, const double* lnA, double hstep, double* ynew, double* err) {
+int orc_step(void* h, const double* y, double P, const double* lnA, double hstep, double* ynew, double* err, int tab) {
   const Mech& m = *static_cast<Mech*>(h);
   ChemSys<double> sys{m, P, lnA};
-  ros4_step(sys, ros4_hw(), y, hstep, ynew, err);
+  ros4_step(sys, tableau_by_id(tab), y, hstep, ynew, err);
   return 0;
 }
 
@@ -749,9 +847,9 @@ int orc_step(void* h, const double* y, double P, const double* lnA, double hstep
 // status/attempts/accepted/rejected per cell (nullable). Threads over cells.
 int orc_integrate(void* hm, int n, double* y, const double* P, const double* lnA, double dt, double rtol,
                   double atol, double* h, int* status, int* attempts, int* accepted, int* rejected,
-                  int max_steps, double h_min, double T_min, int fixed_steps, int nthreads) {
+                  int max_steps, double h_min, double T_min, int fixed_steps, int nthreads, int tab) {
   const Mech& m = *static_cast<Mech*>(hm);
-  const Tableau tb = ros4_hw();
+  const Tableau tb = tableau_by_id(tab);
   IntOpts o;
   o.rtol = rtol; o.atol = atol; o.max_steps = max_steps; o.h_min = h_min; o.T_min = T_min; o.fixed_steps = fixed_steps;
   std::atomic<int> next(0);

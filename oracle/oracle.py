@@ -60,14 +60,14 @@ def _load():
             lib.orc_source_cplx.argtypes = [vp, _dp, vp, C.c_double, vp, vp, _dp, _dp]
             lib.orc_jacobian.argtypes = [vp, C.c_int, _dp, _dp, vp, _dp, C.c_int]
             lib.orc_rates.argtypes = [vp, _dp, C.c_double, vp] + [_dp] * 6
-            lib.orc_tableau.argtypes = [_dp]
-            lib.orc_step_linear.argtypes = [C.c_int, _dp, _dp, C.c_double, _dp, _dp]
+            lib.orc_tableau.argtypes = [C.c_int, _dp]
+            lib.orc_step_linear.argtypes = [C.c_int, _dp, _dp, C.c_double, _dp, _dp, C.c_int]
             lib.orc_integrate_linear.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_double,
-                                                 C.c_double, C.POINTER(C.c_int)]
-            lib.orc_step.argtypes = [vp, _dp, C.c_double, vp, C.c_double, _dp, _dp]
+                                                 C.c_double, C.POINTER(C.c_int), C.c_int]
+            lib.orc_step.argtypes = [vp, _dp, C.c_double, vp, C.c_double, _dp, _dp, C.c_int]
             lib.orc_integrate.argtypes = [vp, C.c_int, _dp, _dp, vp, C.c_double, C.c_double,
                                           C.c_double, vp, vp, vp, vp, vp, C.c_int, C.c_double,
-                                          C.c_double, C.c_int, C.c_int]
+                                          C.c_double, C.c_int, C.c_int, C.c_int]
             lib.orc_integrate_log.argtypes = [vp, _dp, C.c_double, vp, C.c_double, C.c_double,
                                               C.c_double, C.c_double, C.c_int, _dp, C.c_int,
                                               C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -85,27 +85,34 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def tableau() -> dict:
-    out = np.zeros(41)
-    _load().orc_tableau(out)
-    return {"gamma": out[0], "a": out[1:17].reshape(4, 4), "c": out[17:33].reshape(4, 4),
-            "m": out[33:37], "e": out[37:41]}
+ROS4, ROS3, RODAS3, RODAS4 = 0, 1, 2, 3  # the Rosenbrock methods of Table T:solvers
+TABLEAUX = {"ROS4": ROS4, "ROS3": ROS3, "RODAS3": RODAS3, "RODAS4": RODAS4}
 
 
-def step_linear(A, y, h):
+def tableau(tab: int = ROS4) -> dict:
+    """Transformed coefficients of a Rosenbrock method: s stages, a, c (s x s), m, e, gamma."""
+    out = np.zeros(87)
+    _load().orc_tableau(int(tab), out)
+    s = int(out[0])
+    return {"s": s, "order": int(out[1]), "gamma": out[2],
+            "a": out[3:39].reshape(6, 6)[:s, :s], "c": out[39:75].reshape(6, 6)[:s, :s],
+            "m": out[75:81][:s], "e": out[81:87][:s]}
+
+
+def step_linear(A, y, h, tab: int = ROS4):
     A = _f64(A)
     y = _f64(y)
     ynew = np.zeros_like(y)
     err = np.zeros_like(y)
-    _load().orc_step_linear(len(y), A, y, h, ynew, err)
+    _load().orc_step_linear(len(y), A, y, h, ynew, err, int(tab))
     return ynew, err
 
 
-def integrate_linear(A, y, dt, rtol, atol):
+def integrate_linear(A, y, dt, rtol, atol, tab: int = ROS4):
     A = _f64(A)
     y = _f64(y).copy()
     att = C.c_int(0)
-    st = _load().orc_integrate_linear(len(y), A, y, dt, rtol, atol, C.byref(att))
+    st = _load().orc_integrate_linear(len(y), A, y, dt, rtol, atol, C.byref(att), int(tab))
     return y, st, att.value
 
 
@@ -217,15 +224,15 @@ class Mechanism:
         self._lib.orc_rates(self._h, y, float(P), _ptr(lnA), kf, kr, qf, qr, om, Cc)
         return {"kf": kf, "kr": kr, "qf": qf, "qr": qr, "omega": om, "C": Cc}
 
-    def step(self, y, P, h, lnA=None):
+    def step(self, y, P, h, lnA=None, tableau=ROS4):
         y = _f64(y)
         lnA = None if lnA is None else _f64(lnA)
         ynew, err = np.zeros_like(y), np.zeros_like(y)
-        self._lib.orc_step(self._h, y, float(P), _ptr(lnA), float(h), ynew, err)
+        self._lib.orc_step(self._h, y, float(P), _ptr(lnA), float(h), ynew, err, int(tableau))
         return ynew, err
 
     def integrate(self, y, P, dt, rtol=1e-6, atol=1e-10, h=None, lnA=None, max_steps=100000,
-                  h_min=1e-20, T_min=0.0, fixed_steps=0, threads=None):
+                  h_min=1e-20, T_min=0.0, fixed_steps=0, threads=None, tableau=ROS4):
         """Integrate every cell over [0, dt]; returns (y, info dict)."""
         y = _f64(np.atleast_2d(y)).copy()
         n = y.shape[0]
@@ -236,7 +243,7 @@ class Mechanism:
         threads = threads or os.cpu_count() or 1
         self._lib.orc_integrate(self._h, n, y, P, _ptr(lnA), dt, rtol, atol, _ptr(hh), _ptr(st),
                                 _ptr(att), _ptr(acc), _ptr(rej), max_steps, h_min, T_min,
-                                fixed_steps, threads)
+                                fixed_steps, threads, int(tableau))
         return y, {"h": hh, "status": st, "attempts": att, "accepted": acc, "rejected": rej}
 
     def integrate_log(self, y, P, dt, rtol=1e-6, atol=1e-10, h0=0.0, lnA=None, max_steps=100000):

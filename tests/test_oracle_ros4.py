@@ -20,10 +20,10 @@ from oracle import oracle as O
 ATM = 101325.0
 
 
-def untransformed():
-    t = O.tableau()
-    g = t["gamma"]
-    Gamma = np.linalg.inv(np.diag([1 / g] * 4) - t["c"])
+def untransformed(tab=O.ROS4):
+    t = O.tableau(tab)
+    g, s = t["gamma"], t["s"]
+    Gamma = np.linalg.inv(np.diag([1 / g] * s) - t["c"])
     alpha = t["a"] @ Gamma
     b = t["m"] @ Gamma
     bh = (t["m"] - t["e"]) @ Gamma
@@ -46,10 +46,11 @@ def order_residuals(g, Gamma, alpha, b):
     ])
 
 
-def R(z):
-    g, Gamma, alpha, b, _ = untransformed()
+def R(z, tab=O.ROS4):
+    g, Gamma, alpha, b, _ = untransformed(tab)
     B = alpha + Gamma
-    return 1 + z * b @ np.linalg.solve(np.eye(4) - z * B, np.ones(4))
+    s = len(b)
+    return 1 + z * b @ np.linalg.solve(np.eye(s) - z * B, np.ones(s))
 
 
 def test_gamma_constant_and_lower_triangular():
@@ -204,3 +205,66 @@ def test_failure_statuses(omech):
     assert info["status"][0] == O.NONFINITE and info["status"][1] == O.OK
     _, info = m.integrate(y, st.P, 1e-6, T_min=5000.0)
     assert np.all(info["status"] == O.SKIPPED)
+
+
+# ---------------------------------------------------------------- the other methods of Table T:solvers
+# ROS3 and RODAS3 (Sandu et al. 1997), RODAS4 (Hairer & Wanner): order 3(2), 3(2), 4(3).
+OTHERS = [(O.ROS3, 3), (O.RODAS3, 3), (O.RODAS4, 4)]
+NCOND = {2: 2, 3: 4, 4: 8}
+
+
+@pytest.mark.parametrize("tab,order", OTHERS + [(O.ROS4, 4)])
+def test_tableau_order_conditions_all_methods(tab, order):
+    g, Gamma, alpha, b, bh = untransformed(tab)
+    assert O.tableau(tab)["order"] == order
+    assert np.allclose(np.diag(Gamma), g, rtol=0, atol=1e-13)  # (inverse of a 6 x 6 matrix)
+    r = order_residuals(g, Gamma, alpha, b)
+    assert np.abs(r[:NCOND[order]]).max() < 1e-14
+    if order < 4:
+        assert np.abs(r[NCOND[order]:]).max() > 1e-4  # and not of the next order
+    rh = order_residuals(g, Gamma, alpha, bh)
+    assert np.abs(rh[:NCOND[order - 1]]).max() < 1e-14
+
+
+@pytest.mark.parametrize("tab,order", OTHERS)
+def test_l_stability_all_methods(tab, order):
+    for w in np.logspace(-3, 6, 100):
+        assert abs(R(1j * w, tab)) <= 1 + 1e-12
+    assert abs(R(-1e12, tab)) < 1e-10
+
+
+@pytest.mark.parametrize("tab,order", OTHERS)
+def test_one_step_closed_form_all_methods(tab, order):
+    A = np.array([[-1.0, 40.0], [-40.0, -1.0]])
+    h = 0.05
+    y0 = np.array([1.0, -0.5])
+    y1, _ = O.step_linear(A, y0, h, tab)
+    lam, V = np.linalg.eig(A)
+    Rm = (V @ np.diag([R(h * l, tab) for l in lam]) @ np.linalg.inv(V)).real
+    assert np.allclose(y1, Rm @ y0, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("tab,order", OTHERS)
+def test_convergence_order_all_methods(omech, tab, order):
+    m = omech("tiny_hon7.mech")
+    y0 = _tiny_state(m)
+    dt = 2e-5
+    ref, _ = m.integrate(y0, ATM, dt, fixed_steps=8192, tableau=tab)
+    sc = 1e-10 + 1e-6 * np.abs(ref[0])
+    errs = []
+    for K in (32, 64, 128):
+        yk, _ = m.integrate(y0, ATM, dt, fixed_steps=K, tableau=tab)
+        errs.append(np.sqrt(np.mean(((yk[0] - ref[0]) / sc) ** 2)))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(orders - order) < 0.2), orders
+
+
+@pytest.mark.parametrize("tab,order", OTHERS)
+def test_adaptive_all_methods_agree(omech, tab, order):
+    """Every method reaches the same state within its tolerance (tight run as reference)."""
+    m = omech("tiny_hon7.mech")
+    y0 = _tiny_state(m, 1050.0)
+    ref, _ = m.integrate(y0, ATM, 2e-5, rtol=1e-12, atol=1e-20, tableau=O.ROS4)
+    yk, info = m.integrate(y0, ATM, 2e-5, rtol=1e-8, atol=1e-16, tableau=tab)
+    assert info["status"][0] == O.OK
+    assert np.max(np.abs(yk[0] - ref[0]) / (1e-14 + np.abs(ref[0]))) <= 1e-6
