@@ -68,7 +68,14 @@ typedef struct {
   int32_t verbose;     /* print compile logs (register use) to stderr */
   const char* cache_dir; /* directory for compiled cubins; NULL = no disk cache */
   int32_t adjoint;     /* chem_mech_compile_only: compile the adjoint module instead */
+  int32_t tableau;     /* chem_mech_compile_only: Rosenbrock method (CHEM_ROS4 ...) */
 } chem_build_opts;
+
+/* Rosenbrock methods (the solver table of the paper, Table T:solvers) */
+#define CHEM_ROS4 0   /* Hairer-Wanner L-stable, 4 stages, order 4(3): the default */
+#define CHEM_ROS3 1   /* Sandu et al. (1997), 3 stages, order 3(2), L-stable */
+#define CHEM_RODAS3 2 /* Sandu et al. (1997), 4 stages, order 3(2), stiffly accurate */
+#define CHEM_RODAS4 3 /* Hairer-Wanner, 6 stages, order 4(3), stiffly accurate */
 
 /* Options for chem_integrate (NULL = defaults shown). */
 typedef struct {
@@ -81,6 +88,8 @@ typedef struct {
   const double* lnA;   /* device [Nr]: ln of the pre-exponential factors (SI units; for falloff
                           reactions the high-pressure limit); NULL = the mechanism's values */
   int32_t* attempts;   /* device [n_cells] out: step attempts per cell; NULL = not written */
+  int32_t tableau;     /* Rosenbrock method, CHEM_ROS4 (0, default) .. CHEM_RODAS4; the step-size
+                          controller uses err^(-1/order); the adjoint entry points need CHEM_ROS4 */
 } chem_int_opts;
 
 /* Parse a mechanism spec file (format: paper_2205_05681_gb300/synth.py docstring), build its

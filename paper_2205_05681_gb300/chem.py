@@ -32,7 +32,7 @@ CACHE_DIR = os.environ.get("CHEM_CACHE_DIR", os.path.join(os.path.dirname(__file
 
 class BuildOpts(C.Structure):
     _fields_ = [("team", C.c_int32), ("block", C.c_int32), ("verbose", C.c_int32),
-                ("cache_dir", C.c_char_p), ("adjoint", C.c_int32)]
+                ("cache_dir", C.c_char_p), ("adjoint", C.c_int32), ("tableau", C.c_int32)]
 
 
 class TapeStruct(C.Structure):
@@ -43,7 +43,7 @@ class TapeStruct(C.Structure):
 class IntOpts(C.Structure):
     _fields_ = [("max_steps", C.c_int32), ("h_min", C.c_double), ("T_min", C.c_double),
                 ("mode", C.c_int32), ("team", C.c_int32), ("block", C.c_int32),
-                ("lnA", C.c_void_p), ("attempts", C.c_void_p)]
+                ("lnA", C.c_void_p), ("attempts", C.c_void_p), ("tableau", C.c_int32)]
 
 
 _lib = None
@@ -106,12 +106,15 @@ def _check(rc: int):
         raise ChemError("chem error %d: %s" % (rc, library().chem_last_error().decode()))
 
 
+ROS4, ROS3, RODAS3, RODAS4 = 0, 1, 2, 3  # Rosenbrock methods (CHEM_ROS4 ...)
+
+
 def compile_only(spec_path: str, team: int = 0, block: int = 0, cache_dir: Optional[str] = None,
-                 verbose: bool = False, adjoint: bool = False) -> str:
+                 verbose: bool = False, adjoint: bool = False, tableau: int = ROS4) -> str:
     """Generate and NVRTC-compile a mechanism's kernels for sm_103a (no GPU needed)."""
     buf = C.create_string_buffer(1 << 16)
     o = BuildOpts(team, block, int(verbose), cache_dir.encode() if cache_dir else None,
-                  int(adjoint))
+                  int(adjoint), int(tableau))
     _check(library().chem_mech_compile_only(spec_path.encode(), C.byref(o), buf, len(buf)))
     return buf.value.decode(errors="replace")
 
@@ -151,7 +154,7 @@ class Mechanism:
         self._lib = lib
         self.spec_path = spec_path
         h = C.c_void_p()
-        o = BuildOpts(team, block, int(verbose), cache_dir.encode() if cache_dir else None, 0)
+        o = BuildOpts(team, block, int(verbose), cache_dir.encode() if cache_dir else None, 0, 0)
         _check(lib.chem_mech_load(spec_path.encode(), C.byref(o), C.byref(h)))
         self._h = h
         ns, nr, ne = C.c_int32(), C.c_int32(), C.c_int32()
@@ -198,10 +201,10 @@ class Mechanism:
 
     # ------------------------------------------------------------------ integration
     def opts(self, mode=MODE_PERSISTENT, max_steps=0, h_min=0.0, T_min=0.0, team=0, block=0,
-             lnA=None, attempts=None) -> IntOpts:
+             lnA=None, attempts=None, tableau=ROS4) -> IntOpts:
         return IntOpts(max_steps, h_min, T_min, mode, team, block,
                        None if lnA is None else lnA.data_ptr(),
-                       None if attempts is None else attempts.data_ptr())
+                       None if attempts is None else attempts.data_ptr(), int(tableau))
 
     def integrate_workspace(self, n_cells: int, opts: Optional[IntOpts] = None) -> int:
         o = opts or self.opts()

@@ -19,6 +19,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -257,16 +258,83 @@ int read_spec(const char* path, MechData* m) {
 
 // ------------------------------------------------------------------------------ code generation
 
-// Hairer & Wanner L-stable ROS4 (Solving ODEs II, Sec. IV.7) in transformed variables: gamma,
-// a_ij, c_ij, m_i and error weights e_i.  Stage 4 uses the stage-3 argument (a_4j = a_3j).
-struct Ros4Coefficients {
-  double gamma = 0.57282;
-  double a21 = 2.0, a31 = 1.867943637803922, a32 = 0.2344449711399156;
-  double c21 = -7.137615036412310, c31 = 2.580708087951457, c32 = 0.6515950076447975;
-  double c41 = -2.137148994382534, c42 = -0.3214669691237626, c43 = -0.6949742501781779;
-  double m1 = 2.255570073418735, m2 = 0.2870493262186792, m3 = 0.4353179431840180, m4 = 1.093502252409163;
-  double e1 = -0.2815431932141155, e2 = -0.07276199124938920, e3 = -0.1082196201495311, e4 = -1.093502252409163;
+// The Rosenbrock methods of the paper's solver table, in transformed variables (gamma, a_ij,
+// c_ij, m_i, error weights e_i), entered from their publications:
+//   0 ROS4   Hairer & Wanner, Solving ODEs II, Sec. IV.7 (L-stable, order 4(3)) -- the default;
+//   1 ROS3   Sandu et al. (1997), order 3(2), L-stable;
+//   2 RODAS3 Sandu et al. (1997), order 3(2), stiffly accurate;
+//   3 RODAS4 Hairer & Wanner, Sec. VI.4, order 4(3), stiffly accurate.
+struct RosCoefficients {
+  int s = 0, order = 0;
+  double gamma = 0;
+  double a[6][6] = {}, c[6][6] = {}, m[6] = {}, e[6] = {};
 };
+
+RosCoefficients ros_coefficients(int id) {
+  RosCoefficients t;
+  if (id == 1) {
+    t.s = 3; t.order = 3; t.gamma = 0.43586652150845899941601945119356;
+    t.a[1][0] = 1.0; t.a[2][0] = 1.0;
+    t.c[1][0] = -1.0156171083877702091975600115545;
+    t.c[2][0] = 4.0759956452537699824805835358067; t.c[2][1] = 9.2076794298330791242156818474003;
+    t.m[0] = 1.0; t.m[1] = 6.1697947043828245592553615689730; t.m[2] = -0.42772256543218573326238373806514;
+    t.e[0] = 0.5; t.e[1] = -2.9079558716805469821718236208017; t.e[2] = 0.22354069897811569627360909276199;
+  } else if (id == 2) {
+    t.s = 4; t.order = 3; t.gamma = 0.5;
+    t.a[2][0] = 2.0; t.a[3][0] = 2.0; t.a[3][2] = 1.0;
+    t.c[1][0] = 4.0; t.c[2][0] = 1.0; t.c[2][1] = -1.0; t.c[3][0] = 1.0; t.c[3][1] = -1.0; t.c[3][2] = -8.0 / 3.0;
+    t.m[0] = 2.0; t.m[2] = 1.0; t.m[3] = 1.0;
+    t.e[3] = 1.0;
+  } else if (id == 3) {
+    t.s = 6; t.order = 4; t.gamma = 0.25;
+    const double a5[4] = {1.221224509226641, 6.019134481288629, 12.53708332932087, -0.6878860361058950};
+    t.a[1][0] = 1.544;
+    t.a[2][0] = 0.9466785280815826; t.a[2][1] = 0.2557011698983284;
+    t.a[3][0] = 3.314825187068521; t.a[3][1] = 2.896124015972201; t.a[3][2] = 0.9986419139977817;
+    for (int j = 0; j < 4; ++j) { t.a[4][j] = a5[j]; t.a[5][j] = a5[j]; t.m[j] = a5[j]; }
+    t.a[5][4] = 1.0;
+    t.c[1][0] = -5.6688;
+    t.c[2][0] = -2.430093356833875; t.c[2][1] = -0.2063599157091915;
+    t.c[3][0] = -0.1073529058151375; t.c[3][1] = -9.594562251023355; t.c[3][2] = -20.47028614809616;
+    t.c[4][0] = 7.496443313967647; t.c[4][1] = -10.24680431464352; t.c[4][2] = -33.99990352819905;
+    t.c[4][3] = 11.70890893206160;
+    t.c[5][0] = 8.083246795921522; t.c[5][1] = -7.981132988064893; t.c[5][2] = -31.52159432874371;
+    t.c[5][3] = 16.31930543123136; t.c[5][4] = -6.058818238834054;
+    t.m[4] = 1.0; t.m[5] = 1.0;
+    t.e[5] = 1.0;
+  } else {
+    t.s = 4; t.order = 4; t.gamma = 0.57282;
+    t.a[1][0] = 2.0;
+    t.a[2][0] = 1.867943637803922; t.a[2][1] = 0.2344449711399156;
+    t.a[3][0] = 1.867943637803922; t.a[3][1] = 0.2344449711399156;
+    t.c[1][0] = -7.137615036412310;
+    t.c[2][0] = 2.580708087951457; t.c[2][1] = 0.6515950076447975;
+    t.c[3][0] = -2.137148994382534; t.c[3][1] = -0.3214669691237626; t.c[3][2] = -0.6949742501781779;
+    t.m[0] = 2.255570073418735; t.m[1] = 0.2870493262186792; t.m[2] = 0.4353179431840180; t.m[3] = 1.093502252409163;
+    t.e[0] = -0.2815431932141155; t.e[1] = -0.07276199124938920; t.e[2] = -0.1082196201495311;
+    t.e[3] = -1.093502252409163;
+  }
+  return t;
+}
+
+// per stage: 1 = f at a new argument, 0 = the previous stage's argument again, 2 = the argument is y
+std::vector<int> stage_f_reuse(const RosCoefficients& t) {
+  std::vector<int> nf(t.s, 1);
+  for (int i = 1; i < t.s; ++i) {
+    bool zero = true, same = i > 1;
+    for (int j = 0; j < 6; ++j) {
+      zero = zero && t.a[i][j] == 0.0;
+      if (i > 1) same = same && t.a[i][j] == t.a[i - 1][j];
+    }
+    nf[i] = zero ? 2 : (same ? 0 : 1);
+  }
+  return nf;
+}
+
+bool needs_f0(const RosCoefficients& t) {
+  for (int v : stage_f_reuse(t)) if (v == 2) return true;
+  return false;
+}
 
 std::string num(double v) {
   char b[40];
@@ -283,20 +351,31 @@ void emit_array(std::ostringstream& o, const char* type, const char* name, const
   o << "};\n";
 }
 
-std::string emit_mechanism(const MechData& m, int team, int tpb, bool adjoint) {
+std::string emit_mechanism(const MechData& m, int team, int tpb, bool adjoint, int tableau) {
   const int ns = (int)m.sp.size(), nr = (int)m.rx.size();
   std::ostringstream o;
   o << "// generated for mechanism " << m.name << "\n";
   if (adjoint) o << "#define CHEM_ADJOINT 1\n#define CHEM_ADJ_SCRATCH_BYTES " << CHEM_ADJ_SCRATCH_BYTES << "\n";
   o << "#define NS " << ns << "\n#define NR " << nr << "\n#define TEAM " << team << "\n#define TPB " << tpb
     << "\n#define MAXP " << kMaxSide << "\n";
-  Ros4Coefficients c;
-  o << "#define RGAM " << num(c.gamma) << "\n#define RA21 " << num(c.a21) << "\n#define RA31 " << num(c.a31)
-    << "\n#define RA32 " << num(c.a32) << "\n#define RC21 " << num(c.c21) << "\n#define RC31 " << num(c.c31)
-    << "\n#define RC32 " << num(c.c32) << "\n#define RC41 " << num(c.c41) << "\n#define RC42 " << num(c.c42)
-    << "\n#define RC43 " << num(c.c43) << "\n#define RM1 " << num(c.m1) << "\n#define RM2 " << num(c.m2)
-    << "\n#define RM3 " << num(c.m3) << "\n#define RM4 " << num(c.m4) << "\n#define RE1 " << num(c.e1)
-    << "\n#define RE2 " << num(c.e2) << "\n#define RE3 " << num(c.e3) << "\n#define RE4 " << num(c.e4) << "\n";
+  const RosCoefficients c = ros_coefficients(tableau);
+  const std::vector<int> nf = stage_f_reuse(c);
+  o << "#define TABLEAU_ID " << tableau << "\n#define RS " << c.s << "\n#define RORDER " << c.order
+    << "\n#define NEED_F0 " << (needs_f0(c) ? 1 : 0) << "\n#define RGAM " << num(c.gamma) << "\n";
+  emit_array(o, "double", "rk_a", "[" + std::to_string(c.s * c.s) + "]", c.s * c.s,
+             [&](int i) { return num(c.a[i / c.s][i % c.s]); });
+  emit_array(o, "double", "rk_c", "[" + std::to_string(c.s * c.s) + "]", c.s * c.s,
+             [&](int i) { return num(c.c[i / c.s][i % c.s]); });
+  emit_array(o, "double", "rk_m", "[" + std::to_string(c.s) + "]", c.s, [&](int i) { return num(c.m[i]); });
+  emit_array(o, "double", "rk_e", "[" + std::to_string(c.s) + "]", c.s, [&](int i) { return num(c.e[i]); });
+  emit_array(o, "int", "rk_newf", "[" + std::to_string(c.s) + "]", c.s, [&](int i) { return std::to_string(nf[i]); });
+  if (tableau == 0) {  // named ROS4 coefficients used by the adjoint
+    o << "#define RA21 " << num(c.a[1][0]) << "\n#define RA31 " << num(c.a[2][0]) << "\n#define RA32 " << num(c.a[2][1])
+      << "\n#define RC21 " << num(c.c[1][0]) << "\n#define RC31 " << num(c.c[2][0]) << "\n#define RC32 " << num(c.c[2][1])
+      << "\n#define RC41 " << num(c.c[3][0]) << "\n#define RC42 " << num(c.c[3][1]) << "\n#define RC43 " << num(c.c[3][2])
+      << "\n#define RM1 " << num(c.m[0]) << "\n#define RM2 " << num(c.m[1]) << "\n#define RM3 " << num(c.m[2])
+      << "\n#define RM4 " << num(c.m[3]) << "\n";
+  }
   const double Wb = m.sp[ns - 1].W;
   emit_array(o, "double", "mk_W", "[" + std::to_string(ns) + "]", ns, [&](int k) { return num(m.sp[k].W); });
   emit_array(o, "double", "mk_invW", "[" + std::to_string(ns) + "]", ns, [&](int k) { return num(1.0 / m.sp[k].W); });
@@ -465,9 +544,9 @@ const char* const kAdjScratchExpr = "&chem_adj_scratch";
 const char* const kAdjScratchSym = "chem_adj_scratch";
 
 // cubin for (mechanism, team, block): from cache_dir if present, else compiled (and stored)
-int build_cubin(const MechData& m, int team, int tpb, bool adjoint, const char* cache_dir, bool verbose,
+int build_cubin(const MechData& m, int team, int tpb, bool adjoint, int tableau, const char* cache_dir, bool verbose,
                 std::string* cubin, std::string* log) {
-  const std::string src = emit_mechanism(m, team, tpb, adjoint);
+  const std::string src = emit_mechanism(m, team, tpb, adjoint, tableau);
   int major = 0, minor = 0;
   nvrtcVersion(&major, &minor);
   std::string key = src;
@@ -477,8 +556,8 @@ int build_cubin(const MechData& m, int team, int tpb, bool adjoint, const char* 
   snprintf(hex, sizeof(hex), "%016llx", (unsigned long long)fnv1a(key));
   std::string path;
   if (cache_dir && *cache_dir) {
-    path = std::string(cache_dir) + "/" + m.name + (adjoint ? "_adj" : "") + "_t" + std::to_string(team) + "_b" +
-           std::to_string(tpb) + "_" + hex + ".cubin";
+    path = std::string(cache_dir) + "/" + m.name + (adjoint ? "_adj" : "") + "_r" + std::to_string(tableau) + "_t" +
+           std::to_string(team) + "_b" + std::to_string(tpb) + "_" + hex + ".cubin";
     std::ifstream in(path, std::ios::binary);
     if (in) {
       std::ostringstream ss;
@@ -533,8 +612,9 @@ struct chem_mech {
   int default_team = 32, default_tpb = 64;
   std::mutex mu;       // guards modules
   std::mutex host_mu;  // guards the chem_integrate_host buffers
-  std::map<std::pair<int, int>, std::unique_ptr<Module>> modules;      // forward kernels
-  std::map<std::pair<int, int>, std::unique_ptr<Module>> adj_modules;  // + adjoint kernels
+  // keyed by (lanes per cell, threads per block, Rosenbrock method)
+  std::map<std::tuple<int, int, int>, std::unique_ptr<Module>> modules;      // forward kernels
+  std::map<std::tuple<int, int, int>, std::unique_ptr<Module>> adj_modules;  // + adjoint kernels
   // plain-mode host mirror of the activity counter and host-API buffers
   unsigned int* pinned = nullptr;
   CUdeviceptr host_api_buf = 0;
@@ -544,10 +624,10 @@ struct chem_mech {
 namespace {
 
 // shared-memory slots of one cell; mirrors the OFF_* layout of ros4_device.cuh
-int slots_for(const MechData& m) {
-  const int ns = (int)m.sp.size(), nr = (int)m.rx.size();
-  (void)nr;
-  return ns * ns + 17 * ns + 24;
+int slots_for(const MechData& m, int tableau) {
+  const int ns = (int)m.sp.size();
+  const RosCoefficients c = ros_coefficients(tableau);
+  return ns * ns + (13 + c.s + (needs_f0(c) ? 1 : 0)) * ns + 24;
 }
 
 // default kernel configuration by mechanism size (the autotuner's usual pick on GB300):
@@ -564,19 +644,20 @@ int check_config(int team, int tpb) {
   return fail(CHEM_EARG, "unsupported kernel config team=%d block=%d", team, tpb);
 }
 
-int smem_bytes(const MechData& m, int team, int tpb) {
+int smem_bytes(const MechData& m, int team, int tpb, int tableau) {
   const int teams = team == 1 ? tpb : (team == 32 ? tpb / 32 : 1);
-  return slots_for(m) * 8 * teams;
+  return slots_for(m, tableau) * 8 * teams;
 }
 
-int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = false) {
+int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = false, int tableau = 0) {
   std::lock_guard<std::mutex> lk(m->mu);
-  auto key = std::make_pair(team, tpb);
+  if (tableau < 0 || tableau > 3) return fail(CHEM_EARG, "unknown Rosenbrock method %d", tableau);
+  auto key = std::make_tuple(team, tpb, tableau);
   auto& mods = adjoint ? m->adj_modules : m->modules;
   auto it = mods.find(key);
   if (it != mods.end()) { *out = it->second.get(); return 0; }
   if (int rc = check_config(team, tpb)) return rc;
-  const int smem = smem_bytes(m->data, team, tpb);
+  const int smem = smem_bytes(m->data, team, tpb, tableau);
   int max_optin = 0;
   CUdevice dev;
   CU_TRY(drv::cuCtxGetDevice(&dev));
@@ -584,7 +665,8 @@ int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = fal
   if (smem > max_optin)
     return fail(CHEM_EARG, "config team=%d block=%d needs %d B shared memory (max %d)", team, tpb, smem, max_optin);
   std::string cubin, log;
-  if (int rc = build_cubin(m->data, team, tpb, adjoint, m->cache_dir.c_str(), m->verbose, &cubin, &log)) return rc;
+  if (int rc = build_cubin(m->data, team, tpb, adjoint, tableau, m->cache_dir.c_str(), m->verbose, &cubin, &log))
+    return rc;
   auto mod = std::make_unique<Module>();
   mod->team = team;
   mod->tpb = tpb;
@@ -601,8 +683,8 @@ int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = fal
   CU_TRY(drv::cuModuleGetGlobal(&slots_ptr, &slots_sz, mod->mod, "chem_slots"));
   int dev_slots = 0;
   CU_TRY(drv::cuMemcpyDtoH(&dev_slots, slots_ptr, sizeof(int)));
-  if (dev_slots != slots_for(m->data))
-    return fail(CHEM_ECUDA, "shared-memory layout mismatch (%d vs %d)", dev_slots, slots_for(m->data));
+  if (dev_slots != slots_for(m->data, tableau))
+    return fail(CHEM_ECUDA, "shared-memory layout mismatch (%d vs %d)", dev_slots, slots_for(m->data, tableau));
   for (CUfunction f : {mod->f_source, mod->f_jac, mod->f_int, mod->f_pinit, mod->f_patt}) {
     CU_TRY(drv::cuFuncSetAttribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem));
     // all of L1 as shared memory: occupancy is bounded by the cells' shared-memory footprint
@@ -640,7 +722,7 @@ int resolve(chem_mech* m, const chem_int_opts* o, Module** mod) {
     team = o->team;
     tpb = o->block > 0 ? o->block : (team == 1 ? 64 : (team == 32 ? 64 : team));
   }
-  return get_module(m, team, tpb, mod);
+  return get_module(m, team, tpb, mod, false, o ? o->tableau : 0);
 }
 
 int make_current(chem_mech* m) {
@@ -707,7 +789,10 @@ int chem_mech_compile_only(const char* spec_path, const chem_build_opts* opts, c
   std::string cubin, lg;
   const bool adj = opts && opts->adjoint;
   if (adj && team == 1) return fail(CHEM_EARG, "the adjoint needs a multi-lane configuration (team >= 32)");
-  int rc = build_cubin(d, team, tpb, adj, opts ? opts->cache_dir : nullptr, opts && opts->verbose, &cubin, &lg);
+  const int tab = opts ? opts->tableau : 0;
+  if (tab < 0 || tab > 3) return fail(CHEM_EARG, "unknown Rosenbrock method %d", tab);
+  if (adj && tab != 0) return fail(CHEM_EARG, "the adjoint is implemented for ROS4 (tableau 0)");
+  int rc = build_cubin(d, team, tpb, adj, tab, opts ? opts->cache_dir : nullptr, opts && opts->verbose, &cubin, &lg);
   if (log && log_cap) {
     const size_t n = std::min(lg.size(), log_cap - 1);
     memcpy(log, lg.data(), n);
@@ -1002,6 +1087,7 @@ int chem_integrate_ckpt(chem_mech_t m, int64_t n_cells, double* T, const double*
 
 static int adjoint_module(chem_mech_t m, const chem_int_opts* o, Module** mod) {
   Module* fwd;
+  if (o && o->tableau != 0) return fail(CHEM_EARG, "the adjoint is implemented for ROS4 (tableau 0)");
   if (int rc = resolve(m, o, &fwd)) return rc;
   if (fwd->team == 1) return fail(CHEM_EARG, "the adjoint needs a multi-lane configuration (team >= 32)");
   if (int rc = get_module(m, fwd->team, fwd->tpb, mod, true)) return rc;

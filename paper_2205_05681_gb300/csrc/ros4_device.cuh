@@ -74,9 +74,14 @@
 #define OFF_U2 (OFF_F + NEQ)
 #define OFF_U3 (OFF_U2 + NEQ)
 #define OFF_U4 (OFF_U3 + NEQ)
-#define OFF_INVD (OFF_U4 + NEQ)
+#define OFF_INVD (OFF_U2 + (RS - 1) * NEQ)
 #define OFF_TMP (OFF_INVD + NEQ)
+#if NEED_F0
+#define OFF_F0 (OFF_TMP + NEQ)  // f(y) kept for a later stage whose argument is y itself
+#define OFF_C (OFF_F0 + NEQ)
+#else
 #define OFF_C (OFF_TMP + NEQ)
+#endif
 #define OFF_CP (OFF_C + NS)
 #define OFF_HRT (OFF_CP + NS)
 #define OFF_EX (OFF_HRT + NS)
@@ -665,48 +670,61 @@ __device__ void lu_solve(const Team& tm, int ob) {
 
 // ------------------------------------------------------------------------------ ROS4 step
 
-// Hairer-Wanner L-stable ROS4 in transformed variables (coefficients from the generated header:
-// RGAM, RA21, RA31, RA32, RC21, RC31, RC32, RC41, RC42, RC43, RM1..RM4, RE1..RE4; stage 4 is
-// evaluated at the same point as stage 3).
-// One attempt of size hh from y (OFF_Y): y_new into OFF_YT, returns the weighted RMS error
-// (infinity if anything is non-finite).
+// One attempt of the s-stage Rosenbrock method of the generated header (Sec. 2.3, transformed
+// form): coefficients rk_a, rk_c, rk_m, rk_e, gamma RGAM, RS stages; rk_newf[i] says whether stage
+// i needs f at a new argument (1), reuses the previous stage's f (0: equal argument), or uses
+// f(y) (2: the argument is y).  Size hh from y (OFF_Y): y_new into OFF_YT; returns the weighted
+// RMS error (infinity if anything is non-finite).
 __device__ double ros4_attempt(const Team& tm, double P, double hh, double rtol, double atol,
                               const double* lnA_ext) {
-  const int U1 = OFF_U1, U2 = OFF_U2, U3 = OFF_U3, U4 = OFF_U4;
   // stage 1: f0 into U1, M = I/(gamma h) - J
-  eval_f_jac(tm, OFF_Y, U1, P, lnA_ext, -1.0, 1.0 / (RGAM * hh));
+  eval_f_jac(tm, OFF_Y, OFF_U1, P, lnA_ext, -1.0, 1.0 / (RGAM * hh));
+#if NEED_F0
+  for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(OFF_F0, i) = tm.at(OFF_U1, i);
+  tsync();
+#endif
   lu_factor(tm);
-  lu_solve(tm, U1);
+  lu_solve(tm, OFF_U1);
   const double ih = 1.0 / hh;
-  // stage 2
-  for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(OFF_YT, i) = tm.at(OFF_Y, i) + RA21 * tm.at(U1, i);
-  tsync();
-  eval_f(tm, OFF_YT, OFF_F, P, lnA_ext);
-  for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(U2, i) = tm.at(OFF_F, i) + (RC21 * ih) * tm.at(U1, i);
-  tsync();
-  lu_solve(tm, U2);
-  // stage 3 (and 4 at the same point)
-  for (int i = tm.tl; i < NEQ; i += TEAM)
-    tm.at(OFF_YT, i) = tm.at(OFF_Y, i) + RA31 * tm.at(U1, i) + RA32 * tm.at(U2, i);
-  tsync();
-  eval_f(tm, OFF_YT, OFF_F, P, lnA_ext);
-  for (int i = tm.tl; i < NEQ; i += TEAM)
-    tm.at(U3, i) = tm.at(OFF_F, i) + (RC31 * ih) * tm.at(U1, i) + (RC32 * ih) * tm.at(U2, i);
-  tsync();
-  lu_solve(tm, U3);
-  for (int i = tm.tl; i < NEQ; i += TEAM)
-    tm.at(U4, i) = tm.at(OFF_F, i) + (RC41 * ih) * tm.at(U1, i) + (RC42 * ih) * tm.at(U2, i) +
-                   (RC43 * ih) * tm.at(U3, i);
-  tsync();
-  lu_solve(tm, U4);
+#pragma unroll
+  for (int st = 1; st < RS; ++st) {
+    if (rk_newf[st] == 1) {
+      for (int i = tm.tl; i < NEQ; i += TEAM) {
+        double v = tm.at(OFF_Y, i);
+        for (int j = 0; j < st; ++j)
+          if (rk_a[st * RS + j] != 0.0) v += rk_a[st * RS + j] * tm.at(UOFF(j), i);
+        tm.at(OFF_YT, i) = v;
+      }
+      tsync();
+      eval_f(tm, OFF_YT, OFF_F, P, lnA_ext);
+    }
+#if NEED_F0
+    const int of = rk_newf[st] == 2 ? OFF_F0 : OFF_F;
+#else
+    const int of = OFF_F;
+#endif
+    const int ou = UOFF(st);
+    for (int i = tm.tl; i < NEQ; i += TEAM) {
+      double v = tm.at(of, i);
+      for (int j = 0; j < st; ++j)
+        if (rk_c[st * RS + j] != 0.0) v += (rk_c[st * RS + j] * ih) * tm.at(UOFF(j), i);
+      tm.at(ou, i) = v;
+    }
+    tsync();
+    lu_solve(tm, ou);
+  }
   // new state, error estimate and its weighted RMS norm
   double acc = 0.0;
   bool bad = false;
   for (int i = tm.tl; i < NEQ; i += TEAM) {
-    const double u1 = tm.at(U1, i), u2 = tm.at(U2, i), u3 = tm.at(U3, i), u4 = tm.at(U4, i);
     const double y = tm.at(OFF_Y, i);
-    const double yn = y + RM1 * u1 + RM2 * u2 + RM3 * u3 + RM4 * u4;
-    const double e = RE1 * u1 + RE2 * u2 + RE3 * u3 + RE4 * u4;
+    double yn = y, e = 0.0;
+#pragma unroll
+    for (int j = 0; j < RS; ++j) {
+      const double u = tm.at(UOFF(j), i);
+      if (rk_m[j] != 0.0) yn += rk_m[j] * u;  // zero coefficients fold away at compile time
+      if (rk_e[j] != 0.0) e += rk_e[j] * u;
+    }
     tm.at(OFF_YT, i) = yn;
     const double ay = fabs(y), an = fabs(yn);
     const double sc = atol + rtol * (ay > an ? ay : an);
@@ -731,7 +749,7 @@ struct Ctl {
 };
 
 // One attempt plus the controller decision (identical rules to the CPU oracle):
-// fac = clamp(0.9 err^-1/4, 0.2, 6) with err floored at 1e-10 (0.2 if non-finite); accept iff
+// fac = clamp(0.9 err^(-1/order), 0.2, 6) with err floored at 1e-10 (0.2 if non-finite); accept iff
 // err <= 1; no growth right after a rejection; the last step is cut to land on dt (a step
 // within 0.01% of the remainder is stretched to it); h_out is the controller's proposal after
 // the last accepted step, or the proposal that the end cut shortened.
@@ -749,7 +767,11 @@ __device__ __forceinline__ void ros4_advance(const Team& tm, Ctl& c, double P, d
   double fac = 0.2;
   if (finite) {
     const double e = err > 1e-10 ? err : 1e-10;
-    fac = 0.9 / sqrt(sqrt(e));
+#if RORDER == 4
+    fac = 0.9 / sqrt(sqrt(e));  // 0.9 err^(-1/order)
+#else
+    fac = 0.9 / cbrt(e);
+#endif
     fac = fac < 0.2 ? 0.2 : (fac > 6.0 ? 6.0 : fac);
   }
   if (finite && err <= 1.0) {
@@ -995,7 +1017,8 @@ chem_plain_init_k(long long n_cells, const double* __restrict__ T, const double*
   }
 }
 
-extern "C" __global__ void __launch_bounds__(TPB)
+// same register cap as the persistent driver, so that the two differ only in how cells are scheduled
+extern "C" __global__ void __launch_bounds__(TPB, MIN_BLOCKS)
 chem_plain_attempt_k(long long n_cells, double* __restrict__ T, const double* __restrict__ P,
                      double* __restrict__ Y, long long ld, double dt, double rtol, double atol,
                      double* __restrict__ h_out, int* __restrict__ status_out,
@@ -1060,7 +1083,7 @@ extern "C" __global__ void chem_plain_finish_k(long long n_cells, int* __restric
 // initial state, through the ROS4 steps with the accepted step sizes frozen (Sec. 2.3 algebra,
 // differentiated).  Only built for multi-lane teams (contiguous shared-memory layout), and only
 // into the separately compiled adjoint module (CHEM_ADJOINT) so that forward modules compile fast.
-#if TEAM > 1 && defined(CHEM_ADJOINT)
+#if TEAM > 1 && defined(CHEM_ADJOINT) && TABLEAU_ID == 0
 
 // forward-mode dual number: value and one directional derivative
 struct DD {
@@ -1626,7 +1649,7 @@ chem_eval_vjp_k(long long n_cells, const double* __restrict__ T, const double* _
 #endif  // TEAM > 1 && CHEM_ADJOINT
 
 extern "C" __device__ const int chem_aslots =
-#if TEAM > 1 && defined(CHEM_ADJOINT)
+#if TEAM > 1 && defined(CHEM_ADJOINT) && TABLEAU_ID == 0
     ASLOTS;
 #else
     0;

@@ -324,3 +324,25 @@ def test_cuda_graph_of_split_steps(omech, gmech):
         y, info = om.integrate(y, st.P, 1e-6, h=hh, threads=16)
         hh = info["h"]
     assert weighted_norm(y, gpu_state(om, T, Y)).max() <= 1e-4
+
+
+@pytest.mark.parametrize("tab", [1, 2, 3])
+@pytest.mark.parametrize("name", ["h2_13", "ch4_53"])
+def test_other_rosenbrock_methods(omech, gmech, name, tab):
+    """ROS3, RODAS3 and RODAS4 (the other methods of the paper's solver table) against the
+    oracle running the same method, same tolerances as ROS4."""
+    import torch
+    om = omech(name)
+    g = gmech(name, 64, 64)
+    n = {"h2_13": 400, "ch4_53": 80}[name]
+    st, y0 = _inputs(om, name, n, 112 + tab)
+    T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    status = torch.full((n,), -1, dtype=torch.int32, device=T.device)
+    att = torch.zeros(n, dtype=torch.int32, device=T.device)
+    g.integrate(T, P, Y, 1e-6, status=status, opts=g.opts(attempts=att, tableau=tab))
+    assert (status.cpu().numpy() == 0).all()
+    yo, info = om.integrate(y0, st.P, 1e-6, threads=16, tableau=tab)
+    yg = gpu_state(om, T, Y)
+    same = info["attempts"] == att.cpu().numpy()
+    assert same.mean() >= 0.98
+    assert weighted_norm(yo, yg)[same].max() <= 1e-5
