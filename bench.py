@@ -36,6 +36,24 @@ METRIC = "cells integrated/s (ROS4, FP64, rtol 1e-6) vs plain GPU kernel; adjoin
 METHOD_SHAPE = {0: (4, 3), 1: (3, 2), 2: (4, 3), 3: (6, 6)}
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one chem_integrate_k launch on the
+# full bench workload, from a single-pass ncu capture; valid only for the device source they were
+# taken on (sha1 of csrc/ros4_device.cuh), reported as null once that source changes.
+MEASURED_TRAFFIC = {"device_src_sha1": "4c698ec37e4e6b2536adf0bcb3777569447649d1",
+                    "ch4_53_fwd": 30332416 + 1793024,
+                    "ch4_111_batched": 260865792 + 247994368}
+
+
+def measured_traffic(wl, full_size):
+    import hashlib
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2205_05681_gb300",
+                       "csrc", "ros4_device.cuh")
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    if not full_size or sha != MEASURED_TRAFFIC["device_src_sha1"]:
+        return None
+    return MEASURED_TRAFFIC.get(wl)
+
+
 def algorithmic_flops_per_attempt(spec, tableau=0):
     """FP64 operations of one step attempt by the algorithm's own operation counts
     (transcendentals exp/log/log10 counted separately, not folded in):
@@ -352,6 +370,68 @@ def run_reference(args):
     return 0
 
 
+def work_precision(args, chem, synth, torch, np, dev):
+    """Work-precision study of the four Rosenbrock methods, in the manner of the paper's solver
+    verification (Sec. 3.1): rtol = atol = tol for tol in 1e-4 .. 1e-12; per IVP the error norm
+    of Eq. (e:ivp_norm), sqrt(mean_i (|y°_i - y_i| / (1e-10 + 1e-6 |y°_i|))^2) over [T, Y_k],
+    and its maximum over the IVPs, Eq. (e:error_norm).  y° is the oracle's RODAS4 at
+    tol 1e-14 on the first `ref` cells (an independent code path; the paper used CVODEs).
+    Time: CUDA events around one chem_integrate call over all `cells` cells."""
+    from oracle import oracle as O
+    O.build()
+    mech_name, n_all, recipe, seed, dt, _ = synth.WORKLOADS["ch4_53_fwd"]
+    path = synth.mechanism_file(mech_name, MECH_DIR)
+    n = min(args.cells or 4096, n_all)
+    ref_n = min(128, n)
+    st = synth.make_states(synth.mechanism(mech_name), n, recipe, seed)
+    om = O.Mechanism(path)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    y0 = om.state_from_TY(st.T[:ref_n], st.Y[:ref_n])
+    yr, info = om.integrate(y0, st.P[:ref_n], dt, rtol=1e-14, atol=1e-14, threads=cores,
+                            tableau=3)
+    ref_s = time.perf_counter() - t0
+    Tr, Yr = om.TY_from_state(yr)
+    ref = np.concatenate([Tr[:, None], Yr], axis=1)
+    m = chem.Mechanism(path)
+    T0 = torch.tensor(st.T, device=dev)
+    P = torch.tensor(st.P, device=dev)
+    Y0 = torch.tensor(np.ascontiguousarray(st.Y.T), device=dev)
+    att = torch.zeros(n, dtype=torch.int32, device=dev)
+    status = torch.zeros(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for tab, name in enumerate(["ROS4", "ROS3", "RODAS3", "RODAS4"]):
+        o = m.opts(attempts=att, tableau=tab)
+        ws = m.workspace(n, o, device=dev)
+        for e in range(4, 13):
+            tol = 10.0 ** -e
+            times = []
+            for rep in range(2):  # the first run also compiles the method's module
+                T, Y = T0.clone(), Y0.clone()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                m.integrate(T, P, Y, dt, rtol=tol, atol=tol, status=status, opts=o, workspace=ws)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            got = np.concatenate([T[:ref_n].cpu().numpy()[:, None], Y[:, :ref_n].cpu().numpy().T],
+                                 axis=1)
+            ej = np.sqrt(np.mean((np.abs(ref - got) / (1e-10 + 1e-6 * np.abs(ref))) ** 2, axis=1))
+            rows.append({"method": name, "tol": tol, "error": float(ej.max()),
+                         "ms": float(times[-1]), "attempts_mean": float(att.float().mean()),
+                         "ok_cells": int((status == 0).sum())})
+        del ws
+    return {"metric": "work-precision (Eqs. e:ivp_norm, e:error_norm) of ROS4/ROS3/RODAS3/RODAS4",
+            "value": None, "unit": "error norm vs ms", "n_gpus": 1, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "ch4_53_fwd", "cells": n, "error_cells": ref_n, "dt_s": dt,
+                       "reference": "oracle RODAS4, rtol = atol = 1e-14, %d host threads, %.1f s"
+                                    % (cores, ref_s)},
+            "work_precision": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,6 +454,8 @@ def main():
                     help="Rosenbrock method: 0 ROS4 (default), 1 ROS3, 2 RODAS3, 3 RODAS4")
     ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--atol", type=float, default=1e-10)
+    ap.add_argument("--work-precision", action="store_true",
+                    help="error vs time of the four Rosenbrock methods over tolerances 1e-4..1e-12")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -388,6 +470,10 @@ def main():
     torch.cuda.set_device(dev)
 
     wl = args.workload
+    if args.work_precision:
+        if rank == 0:
+            print(json.dumps(work_precision(args, chem, synth, torch, np, dev)), flush=True)
+        return 0
     if wl.endswith("_adjoint"):
         res = adjoint_leg(chem, synth, torch, np, dev, None, wl=wl, cells=args.cells,
                           cap=args.tape_capacity, interval=args.interval)
@@ -576,7 +662,10 @@ def main():
                    "team": cfg["team"], "block": cfg["block"], "smem_bytes": cfg["smem"],
                    "regs": cfg["regs"], "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": measured_traffic(wl, not args.cells and args.tableau == 0),
+                     "traffic_unit": "bytes per launch (one split step)",
+                     "algorithmic_bytes_per_launch": int(8 * n_cells * (2 * (N + 1) + 3)),
                      "kernel": "chem_integrate_k",
                      "peak_source": "measured float64 GEMM (cuBLAS) on this GPU in this run",
                      "flops_per_attempt": fl, "transcendentals_per_attempt": trans},
