@@ -351,7 +351,32 @@ void emit_array(std::ostringstream& o, const char* type, const char* name, const
   o << "};\n";
 }
 
-std::string emit_mechanism(const MechData& m, int team, int tpb, bool adjoint, int tableau) {
+// Kernel order of the reactions: grouped by the branches the reaction code takes (kind, Troe
+// T** term, third-body efficiency count, reactant and product counts and coefficients), stable
+// within a group.  Lanes of a warp take consecutive reactions, so grouped reactions keep the
+// warp on one path; mechanisms that interleave falloff and plain reactions would otherwise pay
+// the falloff branch in almost every warp.  Returns order[kernel index] = mechanism index.
+std::vector<int> kernel_reaction_order(const MechData& m) {
+  std::vector<int> order(m.rx.size());
+  for (size_t r = 0; r < order.size(); ++r) order[r] = (int)r;
+  auto key = [&](int r) {
+    const ReactionData& x = m.rx[r];
+    int neff = 0;
+    if (x.kind != 0)
+      for (auto& e : x.eff) neff += e.second != 1.0;
+    std::vector<int> k = {x.kind, x.kind == 3 && x.troe[3] > 0.0, neff, x.nre, x.npr};
+    for (int i = 0; i < x.nre; ++i) k.push_back(x.rnu[i]);
+    for (int i = 0; i < x.npr; ++i) k.push_back(x.pnu[i]);
+    return k;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
+  return order;
+}
+
+std::string emit_mechanism(const MechData& m0, int team, int tpb, bool adjoint, int tableau) {
+  const std::vector<int> order = kernel_reaction_order(m0);
+  MechData m = m0;
+  for (size_t r = 0; r < order.size(); ++r) m.rx[r] = m0.rx[order[r]];
   const int ns = (int)m.sp.size(), nr = (int)m.rx.size();
   std::ostringstream o;
   o << "// generated for mechanism " << m.name << "\n";
@@ -407,6 +432,7 @@ std::string emit_mechanism(const MechData& m, int team, int tpb, bool adjoint, i
   nasa_table("mk_dcp", 4, [](const double* a, int i) { return a[i + 1] * (i + 1); });
   const std::string R = "[" + std::to_string(nr) + "]";
   const std::string RP = "[" + std::to_string(nr) + "][" + std::to_string(kMaxSide) + "]";
+  emit_array(o, "int", "mk_rorig", R, nr, [&](int r) { return std::to_string(order[r]); });
   emit_array(o, "int", "mk_kind", R, nr, [&](int r) { return std::to_string(m.rx[r].kind); });
   emit_array(o, "double", "mk_lnA", R, nr, [&](int r) { return num(m.rx[r].lnA); });
   emit_array(o, "double", "mk_b", R, nr, [&](int r) { return num(m.rx[r].b); });
@@ -623,11 +649,14 @@ struct chem_mech {
 
 namespace {
 
-// shared-memory slots of one cell; mirrors the OFF_* layout of ros4_device.cuh
-int slots_for(const MechData& m, int tableau) {
+// shared-memory slots of one cell; mirrors the OFF_* layout of ros4_device.cuh: A, Y, U1, YT,
+// U2..Us, [F0], six per-species arrays, the packed permutation (and pivots with one lane per
+// cell), 24 reduction slots
+int slots_for(const MechData& m, int tableau, int team) {
   const int ns = (int)m.sp.size();
   const RosCoefficients c = ros_coefficients(tableau);
-  return ns * ns + (13 + c.s + (needs_f0(c) ? 1 : 0)) * ns + 24;
+  const int packed = (ns + 1) / 2;
+  return ns * ns + (8 + c.s + (needs_f0(c) ? 1 : 0)) * ns + packed * (team == 1 ? 2 : 1) + 24;
 }
 
 // default kernel configuration by mechanism size (the autotuner's usual pick on GB300):
@@ -646,7 +675,7 @@ int check_config(int team, int tpb) {
 
 int smem_bytes(const MechData& m, int team, int tpb, int tableau) {
   const int teams = team == 1 ? tpb : (team == 32 ? tpb / 32 : 1);
-  return slots_for(m, tableau) * 8 * teams;
+  return slots_for(m, tableau, team) * 8 * teams;
 }
 
 int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = false, int tableau = 0) {
@@ -683,8 +712,9 @@ int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = fal
   CU_TRY(drv::cuModuleGetGlobal(&slots_ptr, &slots_sz, mod->mod, "chem_slots"));
   int dev_slots = 0;
   CU_TRY(drv::cuMemcpyDtoH(&dev_slots, slots_ptr, sizeof(int)));
-  if (dev_slots != slots_for(m->data, tableau))
-    return fail(CHEM_ECUDA, "shared-memory layout mismatch (%d vs %d)", dev_slots, slots_for(m->data, tableau));
+  if (dev_slots != slots_for(m->data, tableau, team))
+    return fail(CHEM_ECUDA, "shared-memory layout mismatch (%d vs %d)", dev_slots,
+                slots_for(m->data, tableau, team));
   for (CUfunction f : {mod->f_source, mod->f_jac, mod->f_int, mod->f_pinit, mod->f_patt}) {
     CU_TRY(drv::cuFuncSetAttribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem));
     // all of L1 as shared memory: occupancy is bounded by the cells' shared-memory footprint

@@ -64,39 +64,47 @@
 #define NTEAM 1
 #endif
 
-// per-cell shared-memory slots (units of SS doubles).  The six per-species arrays that only the
-// Jacobian assembly uses (DCP .. JT) alias the stage vectors YT, F, U2..U4, INVD, TMP, which are
-// dead while the Jacobian is formed (it is the first thing a step attempt computes).
+// per-cell shared-memory slots (units of SS doubles), sized so that eight 53-species cells fit
+// in one SM's shared memory:
+// * f at a stage argument overwrites the argument (OFF_F = OFF_YT): the argument is dead once
+//   the concentrations and thermo are formed from it;
+// * the three per-species arrays only the Jacobian assembly uses alias YT, U2, U3, which are
+//   dead while the Jacobian is formed (it is the first thing a step attempt computes); the
+//   chain rule writes JT over DOMT and BE over BK in place;
+// * the LU keeps 1/U_kk on the diagonal of A, and the row permutation is packed two ints per
+//   slot (the single-lane layout also keeps the pivot sequence).
 #define OFF_A 0
 #define OFF_Y (OFF_A + NEQ * NEQ)
 #define OFF_U1 (OFF_Y + NEQ)
 #define OFF_YT (OFF_U1 + NEQ)
-#define OFF_F (OFF_YT + NEQ)
-#define OFF_U2 (OFF_F + NEQ)
+#define OFF_F OFF_YT
+#define OFF_U2 (OFF_YT + NEQ)
 #define OFF_U3 (OFF_U2 + NEQ)
 #define OFF_U4 (OFF_U3 + NEQ)
-#define OFF_INVD (OFF_U2 + (RS - 1) * NEQ)
-#define OFF_TMP (OFF_INVD + NEQ)
 #if NEED_F0
-#define OFF_F0 (OFF_TMP + NEQ)  // f(y) kept for a later stage whose argument is y itself
+#define OFF_F0 (OFF_U2 + (RS - 1) * NEQ)  // f(y) kept for a later stage whose argument is y itself
 #define OFF_C (OFF_F0 + NEQ)
 #else
-#define OFF_C (OFF_TMP + NEQ)
+#define OFF_C (OFF_U2 + (RS - 1) * NEQ)
 #endif
 #define OFF_CP (OFF_C + NS)
 #define OFF_HRT (OFF_CP + NS)
 #define OFF_EX (OFF_HRT + NS)
 #define OFF_IEX (OFF_EX + NS)
 #define OFF_OM (OFF_IEX + NS)
-#define OFF_DCP OFF_YT
-#define OFF_DOMT (OFF_DCP + NS)
+#define OFF_DOMT OFF_YT
 #define OFF_BK (OFF_DOMT + NS)
 #define OFF_AL (OFF_BK + NS)
-#define OFF_BE (OFF_AL + NS)
-#define OFF_JT (OFF_BE + NS)
+#define OFF_JT OFF_DOMT
+#define OFF_BE OFF_BK
+#define PACKED_INTS(n) (((n) + 1) / 2)
+#if TEAM == 1
 #define OFF_PIV (OFF_OM + NS)
-#define OFF_PERM (OFF_PIV + NEQ)
-#define OFF_RED (OFF_PERM + NEQ)
+#define OFF_PERM (OFF_PIV + PACKED_INTS(NEQ))
+#else
+#define OFF_PERM (OFF_OM + NS)
+#endif
+#define OFF_RED (OFF_PERM + PACKED_INTS(NEQ))
 #define SLOTS (OFF_RED + 24)
 #define UOFF(i) ((i) == 0 ? OFF_U1 : OFF_U2 + ((i) - 1) * NEQ)
 
@@ -115,8 +123,16 @@ struct Team {
   int tl;        // lane within the team
   __device__ __forceinline__ double& at(int o, int i) const { return base[(o + i) * SS]; }
   __device__ __forceinline__ double& A(int i, int j) const { return base[(OFF_A + i * NEQ + j) * SS]; }
-  __device__ __forceinline__ int& piv(int i) const { return *reinterpret_cast<int*>(&base[(OFF_PIV + i) * SS]); }
-  __device__ __forceinline__ int& perm(int i) const { return *reinterpret_cast<int*>(&base[(OFF_PERM + i) * SS]); }
+#if TEAM == 1
+  __device__ __forceinline__ int& piv(int i) const {
+    return reinterpret_cast<int*>(&base[(OFF_PIV + (i >> 1)) * SS])[i & 1];
+  }
+#endif
+  __device__ __forceinline__ int& perm(int i) const {
+    return reinterpret_cast<int*>(&base[(OFF_PERM + (i >> 1)) * SS])[i & 1];
+  }
+  // 1/U_kk of the factorised matrix, kept on its diagonal
+  __device__ __forceinline__ double& invd(int k) const { return A(k, k); }
 };
 
 // sum over the team; every lane gets the same bits (butterfly with commutative adds)
@@ -241,7 +257,6 @@ __device__ __forceinline__ void thermo_conc(const Team& tm, int oy, double P, Ce
     if (WJ) {
       const double* d = mk_dcp[k][r];
       const double dcp = d[0] + T * (d[1] + T * (d[2] + T * d[3]));
-      tm.at(OFF_DCP, k) = dcp;
       dcpm += n * dcp;
     }
   }
@@ -272,7 +287,7 @@ __device__ __forceinline__ void reaction_loop(const Team& tm, const CellScalars&
   const double irtp = PATM_OVER_R * invT;
   for (int r = tm.tl; r < NR; r += TEAM) {
     const int kind = mk_kind[r];
-    const double lA = lnA_ext ? lnA_ext[r] : mk_lnA[r];
+    const double lA = lnA_ext ? lnA_ext[mk_rorig[r]] : mk_lnA[r];
     const double kinf = exp(lA + mk_b[r] * lnT - mk_th[r] * invT);
     double kf = kinf;
     double dlkf_dT = 0.0, dlkf_dM = 0.0;
@@ -541,8 +556,8 @@ __device__ void eval_f_jac(const Team& tm, int oy, int of, double P, const doubl
 // ------------------------------------------------------------------------------ LU + solves
 
 // In-place LU with partial pivoting of A (N x N): largest |a| in the column, lowest row on
-// ties.  Row swapped with k at step k in OFF_PIV, 1/U_kk in OFF_INVD, and the composed row
-// permutation (row i of P A is row perm[i] of A) in OFF_PERM for the transposed solves.
+// ties.  1/U_kk replaces U_kk on the diagonal, the composed row permutation (row i of P A is row
+// perm[i] of A) goes to OFF_PERM, and the single-lane layout also keeps the pivot sequence.
 __device__ void lu_factor(const Team& tm) {
 #if TEAM == 1
   for (int k = 0; k < NEQ; ++k) {
@@ -556,7 +571,7 @@ __device__ void lu_factor(const Team& tm) {
     if (p != k)
       for (int j = 0; j < NEQ; ++j) { const double t = tm.A(k, j); tm.A(k, j) = tm.A(p, j); tm.A(p, j) = t; }
     const double inv = 1.0 / tm.A(k, k);
-    tm.at(OFF_INVD, k) = inv;
+    tm.invd(k) = inv;
     for (int i = k + 1; i < NEQ; ++i) {
       const double l = tm.A(i, k) * inv;
       tm.A(i, k) = l;
@@ -603,9 +618,9 @@ __device__ void lu_factor(const Team& tm) {
     // same pipe time whatever its lane count, so the other warps must not repeat the division
     if (tm.tl < 32) {
       const double inv = 1.0 / tm.A(k, k);
+      __syncwarp();  // every lane has read U_kk before lane 0 replaces it by its inverse
       if (tm.tl == 0) {
-        tm.piv(k) = p;
-        tm.at(OFF_INVD, k) = inv;
+        tm.invd(k) = inv;
         if (p != k) { const int t = tm.perm(k); tm.perm(k) = tm.perm(p); tm.perm(p) = t; }
       }
       for (int i = k + 1 + tm.tl; i < NEQ; i += 32) tm.A(i, k) *= inv;
@@ -643,7 +658,7 @@ __device__ void lu_solve(const Team& tm, int ob) {
   for (int i = NEQ - 1; i >= 0; --i) {
     double s = tm.at(ob, i);
     for (int j = i + 1; j < NEQ; ++j) s -= tm.A(i, j) * tm.at(ob, j);
-    tm.at(ob, i) = s * tm.at(OFF_INVD, i);
+    tm.at(ob, i) = s * tm.invd(i);
   }
 #else
   // One warp, the vector in registers: lane l holds rows l, l + 32, ... (NB chunks).  Each
@@ -682,7 +697,7 @@ __device__ void lu_solve(const Team& tm, int ob) {
       for (int kk = 31; kk >= 0; --kk) {
         const int k = kb * 32 + kk;
         if (k < NEQ) {
-          const double xk = __shfl_sync(0xffffffffu, xr[kb], kk) * tm.at(OFF_INVD, k);
+          const double xk = __shfl_sync(0xffffffffu, xr[kb], kk) * tm.invd(k);
           if (ln == kk) xr[kb] = xk;
 #pragma unroll
           for (int c = 0; c <= kb; ++c) {
@@ -708,11 +723,20 @@ __device__ void lu_solve(const Team& tm, int ob) {
 __device__ void lu_solve_col(const Team& tm, int ob) {
   if (tm.tl < 32) {
     const int ln = tm.tl & 31;
-    if (ln == 0)
-      for (int k = 0; k < NEQ; ++k) {
-        const int p = tm.piv(k);
-        if (p != k) { const double t = tm.at(ob, k); tm.at(ob, k) = tm.at(ob, p); tm.at(ob, p) = t; }
+    {  // P b through the composed permutation
+      double g[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        const int i = ln + 32 * c;
+        g[c] = i < NEQ ? tm.at(ob, tm.perm(i)) : 0.0;
       }
+      __syncwarp();
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        const int i = ln + 32 * c;
+        if (i < NEQ) tm.at(ob, i) = g[c];
+      }
+    }
     __syncwarp();
     for (int k = 0; k < NEQ - 1; ++k) {
       const double xk = tm.at(ob, k);
@@ -720,7 +744,7 @@ __device__ void lu_solve_col(const Team& tm, int ob) {
       __syncwarp();
     }
     for (int k = NEQ - 1; k >= 0; --k) {
-      const double xk = tm.at(ob, k) * tm.at(OFF_INVD, k);
+      const double xk = tm.at(ob, k) * tm.invd(k);
       __syncwarp();
       if (ln == (k & 31)) tm.at(ob, k) = xk;
       for (int i = ln; i < k; i += 32) tm.at(ob, i) -= tm.A(i, k) * xk;
@@ -984,10 +1008,10 @@ chem_eval_jacobian_k(long long n_cells, const double* __restrict__ T, const doub
 // Persistent driver: each team pulls cells from the queue counter and integrates them to dt.
 // With TEAM == 1 each thread refills independently (per-lane refill of retired cells); the
 // loop body is one step attempt so that lanes on different cells still execute it together.
-// Registers capped so that the cells that fit in shared memory can all be resident: seven
-// 64-lane teams (53 species) or two 256-lane teams (111 species) per SM (GB300, 53 species:
-// 24.2K vs 22.7K cells/s with the cap)
-#define MIN_BLOCKS (TEAM == 64 ? 7 : (TEAM >= 128 ? 2 : 1))
+// Registers capped so that the cells that fit in shared memory can all be resident: eight
+// 64-lane teams (53 species) or two 256-lane teams (111 species) per SM (GB300, 53 species
+// at seven teams: 24.2K vs 22.7K cells/s with the cap)
+#define MIN_BLOCKS (TEAM == 64 ? 8 : (TEAM >= 128 ? 2 : 1))
 extern "C" __global__ void __launch_bounds__(TPB, MIN_BLOCKS)
 chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __restrict__ P,
                  double* __restrict__ Y, long long ld, double dt, double rtol, double atol,
@@ -1221,7 +1245,8 @@ __device__ __forceinline__ double shfl_xor(double a, int o) { return __shfl_xor_
 #define AOFF_Y3 (AOFF_Y2 + NEQ)
 #define AOFF_V (AOFF_Y3 + NEQ)
 #define AOFF_GP (AOFF_V + NEQ)
-#define AOFF_S (AOFF_GP + NR)
+#define AOFF_TMP (AOFF_GP + NR)
+#define AOFF_S (AOFF_TMP + NEQ)
 // S-typed (2 doubles each) scratch of the VJP: state, gy, C, hRT, cp, ex, iex, dcp, atilde, Cbar,
 // omega (11 x NS) and q (NR), plus 8 reduction slots
 #define VS_Y 0
@@ -1319,7 +1344,7 @@ __device__ void vjp(const Team& tm, double P, const double* __restrict__ lnA_ext
   S Tbar = Z, Bbar = Z;
   for (int r = tm.tl; r < NR; r += TEAM) {
     const int kind = mk_kind[r];
-    const double lA = lnA_ext ? lnA_ext[r] : mk_lnA[r];
+    const double lA = lnA_ext ? lnA_ext[mk_rorig[r]] : mk_lnA[r];
     const S kinf = exp(lA + mk_b[r] * lnT - mk_th[r] * invT);
     S kf = kinf;
     S dlkf_dT = (mk_b[r] + mk_th[r] * invT) * invT;
@@ -1466,21 +1491,21 @@ __device__ void vjp(const Team& tm, double P, const double* __restrict__ lnA_ext
 __device__ void lu_solve_T(const Team& tm, int ob) {
   if (tm.tl < 32) {
     const int ln = tm.tl;
-    for (int i = ln; i < NEQ; i += 32) tm.at(OFF_TMP, i) = tm.at(ob, i);
+    for (int i = ln; i < NEQ; i += 32) tm.at(AOFF_TMP, i) = tm.at(ob, i);
     __syncwarp();
     for (int i = 0; i < NEQ; ++i) {
-      const double zi = tm.at(OFF_TMP, i) * tm.at(OFF_INVD, i);
+      const double zi = tm.at(AOFF_TMP, i) * tm.invd(i);
       __syncwarp();
-      if (ln == (i & 31)) tm.at(OFF_TMP, i) = zi;
-      for (int k = i + 1 + ln; k < NEQ; k += 32) tm.at(OFF_TMP, k) -= tm.A(i, k) * zi;
+      if (ln == (i & 31)) tm.at(AOFF_TMP, i) = zi;
+      for (int k = i + 1 + ln; k < NEQ; k += 32) tm.at(AOFF_TMP, k) -= tm.A(i, k) * zi;
       __syncwarp();
     }
     for (int i = NEQ - 1; i > 0; --i) {
-      const double ti = tm.at(OFF_TMP, i);
-      for (int k = ln; k < i; k += 32) tm.at(OFF_TMP, k) -= tm.A(i, k) * ti;
+      const double ti = tm.at(AOFF_TMP, i);
+      for (int k = ln; k < i; k += 32) tm.at(AOFF_TMP, k) -= tm.A(i, k) * ti;
       __syncwarp();
     }
-    for (int i = ln; i < NEQ; i += 32) tm.at(ob, tm.perm(i)) = tm.at(OFF_TMP, i);
+    for (int i = ln; i < NEQ; i += 32) tm.at(ob, tm.perm(i)) = tm.at(AOFF_TMP, i);
   }
   tsync();
 }
@@ -1639,7 +1664,9 @@ __device__ __forceinline__ long long team_global_id() {
 // accepted steps are recomputed from their checkpoint (states kept in this team's slice of
 // `seg`), then stepped through backwards.  dL/dlnA is accumulated per team and written to
 // gp_partial[team][r]; chem_adjoint_reduce_k sums the teams in a fixed order.
-extern "C" __global__ void __launch_bounds__(TPB)
+// (one block per SM as the register bound: the adjoint's shared memory already limits residency
+// to four 64-lane or one 256-lane team per SM, so the registers go to avoiding spills)
+extern "C" __global__ void __launch_bounds__(TPB, 1)
 chem_adjoint_k(long long n_cells, const double* __restrict__ P, const double* __restrict__ gT,
                const double* __restrict__ gY, long long ld, double* __restrict__ gT0,
                double* __restrict__ gY0, const double* __restrict__ lnA_ext,
@@ -1699,7 +1726,7 @@ extern "C" __global__ void chem_adjoint_reduce_k(long long n_parts, const double
   if (r >= NR) return;
   double s = 0.0;
   for (long long t = 0; t < n_parts; ++t) s += gp_partial[t * NR + r];
-  g_lnA[r] = s;
+  g_lnA[mk_rorig[r]] = s;  // mechanism order
 }
 
 // Vector-Jacobian products per cell (parity entry point of the adjoint's building block):
@@ -1721,7 +1748,7 @@ chem_eval_vjp_k(long long n_cells, const double* __restrict__ T, const double* _
     vjp<double>(tm, P[c], lnA_ext);
     const double* g = reinterpret_cast<const double*>(&tm.base[AOFF_S]) + VS_GY;
     for (int i = tm.tl; i < NEQ; i += TEAM) gy[i * ld + c] = g[i];
-    for (int r = tm.tl; r < NR; r += TEAM) gp[(long long)r * ld + c] = tm.at(AOFF_GP, r);
+    for (int r = tm.tl; r < NR; r += TEAM) gp[(long long)mk_rorig[r] * ld + c] = tm.at(AOFF_GP, r);
     tsync();
   }
 }

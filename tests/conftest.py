@@ -48,3 +48,29 @@ def omech(mech_path):
 def states(name, n, recipe, seed):
     from paper_2205_05681_gb300 import synth
     return synth.make_states(synth.mechanism(name), n, recipe, seed)
+
+
+def shuffled_spec(src, dst, seed):
+    """Copy a mechanism spec with its reactions (each R line with its EFF/LOW/TROE lines) in a
+    seeded random order; returns perm with new reaction i = old reaction perm[i]."""
+    lines = open(src).read().splitlines()
+    head = []
+    blocks = []
+    tail = []
+    i = 0
+    while not lines[i].startswith("REACTIONS"):
+        head.append(lines[i])
+        i += 1
+    head.append(lines[i])
+    i += 1
+    while i < len(lines) and not lines[i].startswith("END"):
+        if lines[i].startswith("R "):
+            blocks.append([lines[i]])
+        elif lines[i].strip() and not lines[i].startswith("#"):
+            blocks[-1].append(lines[i])
+        i += 1
+    tail = lines[i:]
+    perm = np.random.default_rng(seed).permutation(len(blocks))
+    with open(dst, "w") as fh:
+        fh.write("\n".join(head + [l for p in perm for l in blocks[p]] + tail) + "\n")
+    return perm

@@ -14,7 +14,7 @@ Tolerances (stated, from the problem statement's bounds):
 import numpy as np
 import pytest
 
-from tests.conftest import states
+from tests.conftest import shuffled_spec, states
 from tests.gpu_helpers import gpu_mech, gpu_state, gross_f, to_dev, weighted_norm
 
 pytestmark = pytest.mark.gpu
@@ -346,3 +346,39 @@ def test_other_rosenbrock_methods(omech, gmech, name, tab):
     same = info["attempts"] == att.cpu().numpy()
     assert same.mean() >= 0.98
     assert weighted_norm(yo, yg)[same].max() <= 1e-5
+
+
+def test_interleaved_reaction_order(mech_dir, mech_path):
+    """A file with reactions of every kind interleaved: the library runs them in its own
+    branch-grouped kernel order and maps run-time ln A, the per-reaction VJP rows and the
+    integration back to the file's order (oracle on the same file)."""
+    import os
+    import torch
+    from oracle import oracle as O
+    dst = os.path.join(mech_dir, "ch4_53_interleaved.mech")
+    shuffled_spec(mech_path("ch4_53"), dst, 11)
+    om = O.Mechanism(dst)
+    g = gpu_mech(dst, team=64, block=64)
+    st = states("ch4_53", 96, "ch4_partial", 131)
+    y = om.state_from_TY(st.T, st.Y)
+    lnA = om.lnA + np.random.default_rng(3).normal(0.0, 0.2, om.nr)
+    f = g.eval_source(to_dev(y[:, 0]), to_dev(st.P), to_dev(y[:, 1:].T), lnA=to_dev(lnA))
+    f = f.cpu().numpy().T
+    fo = om.source(y, st.P, lnA=lnA)
+    for c in range(len(y)):
+        err = np.abs(f[c] - fo[c]) / (np.abs(fo[c]) + gross_f(om, y[c], st.P[c]) + 1e-300)
+        assert err.max() <= 1e-12, (c, err.max())
+    T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    att = torch.zeros(len(y), dtype=torch.int32, device=T.device)
+    g.integrate(T, P, Y, 1e-6, opts=g.opts(attempts=att))
+    _check_integration(om, st, y, gpu_state(om, T, Y), att.cpu().numpy(), 1e-6, "interleaved")
+    # (d f / d lnA)^T v rows in file order, against complex step of v^T f
+    v = np.random.default_rng(4).normal(size=y.shape) / np.maximum(np.abs(om.source(y, st.P)), 1e-30)
+    _, gp = g.eval_vjp(to_dev(y[:2, 0]), to_dev(st.P[:2]), to_dev(y[:2, 1:].T), to_dev(v[:2].T))
+    gp = gp.cpu().numpy().T
+    ref = np.zeros(om.nr)
+    for r in range(om.nr):
+        d = np.zeros(om.nr, dtype=complex)
+        d[r] = 1e-30j
+        ref[r] = (v[0] @ om.source_cplx(y[0], st.P[0], lnA=om.lnA + d).imag) / 1e-30
+    assert np.all(np.abs(gp[0] - ref) <= 1e-11 * (np.abs(ref) + 1e-3 * np.abs(ref).max()))
