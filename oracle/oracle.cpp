@@ -423,6 +423,7 @@ struct Tableau {
   double c[6][6];
   double m[6];
   double e[6];
+  bool erk = false;  // explicit Runge-Kutta: u_i = h f(y + sum_j a_ij u_j), no Jacobian, no c, gamma
 };
 
 static Tableau ros4_hw() {
@@ -536,11 +537,36 @@ static Tableau rodas4_hw() {
 }
 
 // Rosenbrock methods of Table T:solvers by id: 0 ROS4 (default), 1 ROS3, 2 RODAS3, 3 RODAS4
+// Runge-Kutta-Fehlberg 4(5) (Fehlberg 1969; Hairer, Norsett and Wanner, Solving ODEs I, Table
+// II.5.1), the explicit solver of the paper's Table T:solvers.  Written in the increment form
+// u_i = h k_i so that it shares y_new = y + sum m_j u_j and the error sum e_j u_j with the
+// Rosenbrock methods.  Reading (the paper does not say which solution is propagated): the
+// fifth-order solution is carried (local extrapolation), the difference to the embedded
+// fourth-order solution is the error estimate, so the controller exponent is 1/5.
+static Tableau rkf45_fehlberg() {
+  Tableau t{};
+  t.s = 6;
+  t.order = 5;
+  t.erk = true;
+  t.gamma = 0.0;
+  t.a[1][0] = 1.0 / 4.0;
+  t.a[2][0] = 3.0 / 32.0; t.a[2][1] = 9.0 / 32.0;
+  t.a[3][0] = 1932.0 / 2197.0; t.a[3][1] = -7200.0 / 2197.0; t.a[3][2] = 7296.0 / 2197.0;
+  t.a[4][0] = 439.0 / 216.0; t.a[4][1] = -8.0; t.a[4][2] = 3680.0 / 513.0; t.a[4][3] = -845.0 / 4104.0;
+  t.a[5][0] = -8.0 / 27.0; t.a[5][1] = 2.0; t.a[5][2] = -3544.0 / 2565.0; t.a[5][3] = 1859.0 / 4104.0;
+  t.a[5][4] = -11.0 / 40.0;
+  const double b5[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+  const double b4[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0};
+  for (int i = 0; i < 6; ++i) { t.m[i] = b5[i]; t.e[i] = b5[i] - b4[i]; }
+  return t;
+}
+
 static Tableau tableau_by_id(int id) {
   switch (id) {
     case 1: return ros3_sandu();
     case 2: return rodas3_sandu();
     case 3: return rodas4_hw();
+    case 4: return rkf45_fehlberg();
     default: return ros4_hw();
   }
 }
@@ -567,9 +593,37 @@ struct LinSys {  // y' = A y
   void jac(const S*, S* J) const { for (int i = 0; i < N * N; ++i) J[i] = A[i]; }
 };
 
-// One ROS4 step of size h from y: ynew and the embedded error vector.
+// One explicit Runge-Kutta step (tb.erk): u_i = h f(y + sum_{j<i} a_ij u_j).
+template <class S, class Sys>
+void erk_step(const Sys& sys, const Tableau& tb, const S* y, double h, S* ynew, S* err) {
+  const int N = sys.n();
+  std::vector<S> u(tb.s * N), Y(N), F(N);
+  for (int i = 0; i < tb.s; ++i) {
+    for (int k = 0; k < N; ++k) {
+      Y[k] = y[k];
+      for (int j = 0; j < i; ++j) Y[k] = Y[k] + tb.a[i][j] * u[j * N + k];
+    }
+    sys.rhs(Y.data(), F.data());
+    for (int k = 0; k < N; ++k) u[i * N + k] = h * F[k];
+  }
+  for (int k = 0; k < N; ++k) {
+    ynew[k] = y[k];
+    err[k] = 0.0;
+    for (int j = 0; j < tb.s; ++j) {
+      ynew[k] = ynew[k] + tb.m[j] * u[j * N + k];
+      err[k] = err[k] + tb.e[j] * u[j * N + k];
+    }
+  }
+}
+
+// One ROS4 step of size h from y: ynew and the embedded error vector (an explicit tableau
+// takes the explicit step).
 template <class S, class Sys>
 void ros4_step(const Sys& sys, const Tableau& tb, const S* y, double h, S* ynew, S* err) {
+  if (tb.erk) {
+    erk_step(sys, tb, y, h, ynew, err);
+    return;
+  }
   const int N = sys.n();
   std::vector<S> J(N * N), M(N * N), u(tb.s * N), Y(N), F(N);
   std::vector<int> piv(N);
@@ -808,9 +862,10 @@ int orc_rates(void* h, const double* y, double P, const double* lnA, double* kf,
   return 0;
 }
 
-// tableau `id`: s, order, gamma, a[6][6], c[6][6], m[6], e[6]  (87 doubles)
+// tableau `id`: s, order, gamma, a[6][6], c[6][6], m[6], e[6], explicit flag  (88 doubles)
 int orc_tableau(int id, double* out) {
   Tableau t = tableau_by_id(id);
+  out[87] = t.erk ? 1.0 : 0.0;
   out[0] = t.s;
   out[1] = t.order;
   out[2] = t.gamma;

@@ -86,17 +86,20 @@ def _f64(a):
 
 
 ROS4, ROS3, RODAS3, RODAS4 = 0, 1, 2, 3  # the Rosenbrock methods of Table T:solvers
-TABLEAUX = {"ROS4": ROS4, "ROS3": ROS3, "RODAS3": RODAS3, "RODAS4": RODAS4}
+RKF45 = 4  # the explicit Runge-Kutta-Fehlberg 4(5) of the same table
+TABLEAUX = {"ROS4": ROS4, "ROS3": ROS3, "RODAS3": RODAS3, "RODAS4": RODAS4, "RKF45": RKF45}
 
 
 def tableau(tab: int = ROS4) -> dict:
-    """Transformed coefficients of a Rosenbrock method: s stages, a, c (s x s), m, e, gamma."""
-    out = np.zeros(87)
+    """Transformed coefficients of a Rosenbrock method: s stages, a, c (s x s), m, e, gamma; for
+    the explicit RKF45 (`explicit` true) a is the Butcher matrix, m and e the weights of the
+    propagated solution and of the error estimate (c, gamma zero)."""
+    out = np.zeros(88)
     _load().orc_tableau(int(tab), out)
     s = int(out[0])
     return {"s": s, "order": int(out[1]), "gamma": out[2],
             "a": out[3:39].reshape(6, 6)[:s, :s], "c": out[39:75].reshape(6, 6)[:s, :s],
-            "m": out[75:81][:s], "e": out[81:87][:s]}
+            "m": out[75:81][:s], "e": out[81:87][:s], "explicit": bool(out[87])}
 
 
 def step_linear(A, y, h, tab: int = ROS4):
