@@ -39,9 +39,9 @@ METHOD_SHAPE = {0: (4, 3), 1: (3, 2), 2: (4, 3), 3: (6, 6)}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one chem_integrate_k launch on the
 # full bench workload, from a single-pass ncu capture; valid only for the device source they were
 # taken on (sha1 of csrc/ros4_device.cuh), reported as null once that source changes.
-MEASURED_TRAFFIC = {"device_src_sha1": "4c698ec37e4e6b2536adf0bcb3777569447649d1",
-                    "ch4_53_fwd": 30332416 + 1793024,
-                    "ch4_111_batched": 260865792 + 247994368}
+MEASURED_TRAFFIC = {"device_src_sha1": "1bd5a2dd7d4abf2e6f60a2dab9daacba26b0705c",
+                    "ch4_53_fwd": 30249984 + 1155328,
+                    "ch4_111_batched": 262685696 + 244890112}
 
 
 def measured_traffic(wl, full_size):

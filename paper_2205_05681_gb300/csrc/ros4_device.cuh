@@ -521,6 +521,9 @@ __device__ void eval_f_jac(const Team& tm, int oy, int of, double P, const doubl
   // T sum_k (h_k/RT) J_kT; d cpm/dn_j = cp_j - w_j cp_bath, d cpm/dT = sum_k n_k dcp_k/dT.
   const double hb = tm.at(OFF_HRT, BATH), alb = tm.at(OFF_AL, BATH), beb = tm.at(OFF_BE, BATH);
   const double icpm = 1.0 / cs.cpm;
+  double cpf = 0.0;  // sum_k cp_k omega_k, a team reduction rather than one lane's loop
+  for (int k = tm.tl; k < NS; k += TEAM) cpf += tm.at(OFF_CP, k) * tm.at(OFF_OM, k);
+  cpf = team_sum(tm, cpf);
   for (int l = tm.tl; l < NEQ; l += TEAM) {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int i = 1;
@@ -537,8 +540,6 @@ __device__ void eval_f_jac(const Team& tm, int oy, int of, double P, const doubl
     double val;
     if (l == 0) {
       s += hb * tm.at(OFF_JT, BATH);
-      double cpf = 0.0;
-      for (int k = 0; k < NS; ++k) cpf += tm.at(OFF_CP, k) * tm.at(OFF_OM, k);
       const double dQdT = cpf * V + T * s;
       val = -(dQdT + fT * cs.dcpm) * icpm;
     } else {
