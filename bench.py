@@ -33,15 +33,17 @@ METRIC = "cells integrated/s (ROS4, FP64, rtol 1e-6) vs plain GPU kernel; adjoin
 
 
 # stages and evaluations of f per attempt of each Rosenbrock method: (s, f evaluations incl. f(y))
-METHOD_SHAPE = {0: (4, 3), 1: (3, 2), 2: (4, 3), 3: (6, 6)}
+METHOD_SHAPE = {0: (4, 3), 1: (3, 2), 2: (4, 3), 3: (6, 6), 4: (6, 6)}  # (stages, f evaluations)
+EXPLICIT = {4}  # RKF45: no Jacobian, no factorisation, no solves
+METHODS = ["ROS4", "ROS3", "RODAS3", "RODAS4", "RKF45"]
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one chem_integrate_k launch on the
 # full bench workload, from a single-pass ncu capture; valid only for the device source they were
 # taken on (sha1 of csrc/ros4_device.cuh), reported as null once that source changes.
-MEASURED_TRAFFIC = {"device_src_sha1": "1bd5a2dd7d4abf2e6f60a2dab9daacba26b0705c",
-                    "ch4_53_fwd": 30249984 + 1155328,
-                    "ch4_111_batched": 262685696 + 244890112}
+MEASURED_TRAFFIC = {"device_src_sha1": "e0d474acdd2bfe7ddc63a5c3c63de45781257898",
+                    "ch4_53_fwd": 30329600 + 1221376,
+                    "ch4_111_batched": 261532672 + 243226624}
 
 
 def measured_traffic(wl, full_size):
@@ -61,11 +63,12 @@ def algorithmic_flops_per_attempt(spec, tableau=0):
       and per evaluation of f: thermo 27 per species, 4 + 2*(orders) + 2*(species entries) per
       reaction (+2 per efficiency entry and +2 for third-body/falloff reactions, +12 for the
       falloff blend, +40 for Troe); the Jacobian adds per reaction 2 p^2 + 10 (+2 per efficiency
-      entry x participant) for its p participants.  ROS4 evaluates f at 3 points (stage 4 reuses
+      entry x participant) for its p participants.  RKF45: six evaluations of f and the stage
+      combinations only.  ROS4 evaluates f at 3 points (stage 4 reuses
       stage 3's argument)."""
     s, nf = METHOD_SHAPE[tableau]
     N = spec["ns"]
-    fl = 2.0 * N ** 3 / 3.0 + s * 2.0 * N ** 2 + 6.0 * N ** 2
+    fl = 0.0 if tableau in EXPLICIT else 2.0 * N ** 3 / 3.0 + s * 2.0 * N ** 2 + 6.0 * N ** 2
     f_eval = 27.0 * N
     jac = 0.0
     trans_f = N + 1  # exp per species + log T
@@ -83,6 +86,9 @@ def algorithmic_flops_per_attempt(spec, tableau=0):
             trans_f += 6
         p = len(r["rnu"]) + len(r["pnu"])
         jac += 2 * p * p + 10 + (2 * r["neff"] * p if r["kind"] != "ELEM" else 0)
+    if tableau in EXPLICIT:
+        jac = 0.0
+        fl += 2.0 * s * N  # the stage combinations
     total = fl + nf * f_eval + jac
     return total, nf * trans_f
 
@@ -360,7 +366,7 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl, "mechanism": mech_name, "cells": n_cells, "dt_s": dt,
                        "split_steps_per_step": splits,
-                       "method": ["ROS4", "ROS3", "RODAS3", "RODAS4"][args.tableau],
+                       "method": METHODS[args.tableau],
                        "rtol": args.rtol, "atol": args.atol},
             "cpu_baseline": {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
@@ -451,7 +457,7 @@ def main():
     ap.add_argument("--tape-capacity", type=int, default=4096, help="adjoint workloads: steps/cell")
     ap.add_argument("--interval", type=int, default=16, help="adjoint workloads: checkpoint interval")
     ap.add_argument("--tableau", type=int, default=0,
-                    help="Rosenbrock method: 0 ROS4 (default), 1 ROS3, 2 RODAS3, 3 RODAS4")
+                    help="method: 0 ROS4 (default), 1 ROS3, 2 RODAS3, 3 RODAS4, 4 RKF45 (explicit)")
     ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--atol", type=float, default=1e-10)
     ap.add_argument("--work-precision", action="store_true",
@@ -656,7 +662,7 @@ def main():
         "config": {"workload": wl, "mechanism": mech_name, "species": N,
                    "reactions": len(spec["reactions"]), "cells": n_cells, "dt_s": dt,
                    "split_steps_per_step": splits,
-                   "method": ["ROS4", "ROS3", "RODAS3", "RODAS4"][args.tableau],
+                   "method": METHODS[args.tableau],
                    "cuda_graph": splits > 1,
                    "rtol": args.rtol, "atol": args.atol, "l2": "flushed (512 MiB write) between steps",
                    "team": cfg["team"], "block": cfg["block"], "smem_bytes": cfg["smem"],

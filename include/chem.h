@@ -68,7 +68,7 @@ typedef struct {
   int32_t verbose;     /* print compile logs (register use) to stderr */
   const char* cache_dir; /* directory for compiled cubins; NULL = no disk cache */
   int32_t adjoint;     /* chem_mech_compile_only: compile the adjoint module instead */
-  int32_t tableau;     /* chem_mech_compile_only: Rosenbrock method (CHEM_ROS4 ...) */
+  int32_t tableau;     /* chem_mech_compile_only: integration method (CHEM_ROS4 ...) */
 } chem_build_opts;
 
 /* Rosenbrock methods (the solver table of the paper, Table T:solvers) */
@@ -76,6 +76,11 @@ typedef struct {
 #define CHEM_ROS3 1   /* Sandu et al. (1997), 3 stages, order 3(2), L-stable */
 #define CHEM_RODAS3 2 /* Sandu et al. (1997), 4 stages, order 3(2), stiffly accurate */
 #define CHEM_RODAS4 3 /* Hairer-Wanner, 6 stages, order 4(3), stiffly accurate */
+/* The explicit solver of the same table: Runge-Kutta-Fehlberg 4(5), 6 evaluations of f per step,
+ * no Jacobian or factorisation; the fifth-order solution is propagated (error estimate = its
+ * difference to the fourth-order one, controller exponent 1/5).  For non-stiff cells only: on
+ * stiff chemistry its stable step sizes are tiny and cells end with CHEM_STATUS_MAX_STEPS. */
+#define CHEM_RKF45 4
 
 /* Options for chem_integrate (NULL = defaults shown). */
 typedef struct {
@@ -88,7 +93,7 @@ typedef struct {
   const double* lnA;   /* device [Nr]: ln of the pre-exponential factors (SI units; for falloff
                           reactions the high-pressure limit); NULL = the mechanism's values */
   int32_t* attempts;   /* device [n_cells] out: step attempts per cell; NULL = not written */
-  int32_t tableau;     /* Rosenbrock method, CHEM_ROS4 (0, default) .. CHEM_RODAS4; the step-size
+  int32_t tableau;     /* method, CHEM_ROS4 (0, default) .. CHEM_RODAS4, or CHEM_RKF45; the step-size
                           controller uses err^(-1/order); the adjoint entry points need CHEM_ROS4 */
 } chem_int_opts;
 

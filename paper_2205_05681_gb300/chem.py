@@ -107,6 +107,7 @@ def _check(rc: int):
 
 
 ROS4, ROS3, RODAS3, RODAS4 = 0, 1, 2, 3  # Rosenbrock methods (CHEM_ROS4 ...)
+RKF45 = 4  # explicit Runge-Kutta-Fehlberg 4(5) (CHEM_RKF45), for non-stiff cells
 
 
 def compile_only(spec_path: str, team: int = 0, block: int = 0, cache_dir: Optional[str] = None,

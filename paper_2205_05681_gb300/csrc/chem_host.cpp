@@ -268,10 +268,26 @@ struct RosCoefficients {
   int s = 0, order = 0;
   double gamma = 0;
   double a[6][6] = {}, c[6][6] = {}, m[6] = {}, e[6] = {};
+  bool erk = false;  // explicit Runge-Kutta in increment form u_i = h f(y + sum a_ij u_j)
 };
 
 RosCoefficients ros_coefficients(int id) {
   RosCoefficients t;
+  if (id == 4) {
+    // Runge-Kutta-Fehlberg 4(5): the fifth-order weights are propagated, their difference to the
+    // fourth-order ones is the error estimate (controller exponent 1/5)
+    t.s = 6; t.order = 5; t.erk = true;
+    t.a[1][0] = 1.0 / 4.0;
+    t.a[2][0] = 3.0 / 32.0; t.a[2][1] = 9.0 / 32.0;
+    t.a[3][0] = 1932.0 / 2197.0; t.a[3][1] = -7200.0 / 2197.0; t.a[3][2] = 7296.0 / 2197.0;
+    t.a[4][0] = 439.0 / 216.0; t.a[4][1] = -8.0; t.a[4][2] = 3680.0 / 513.0; t.a[4][3] = -845.0 / 4104.0;
+    t.a[5][0] = -8.0 / 27.0; t.a[5][1] = 2.0; t.a[5][2] = -3544.0 / 2565.0; t.a[5][3] = 1859.0 / 4104.0;
+    t.a[5][4] = -11.0 / 40.0;
+    const double b5[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+    const double b4[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0};
+    for (int i = 0; i < 6; ++i) { t.m[i] = b5[i]; t.e[i] = b5[i] - b4[i]; }
+    return t;
+  }
   if (id == 1) {
     t.s = 3; t.order = 3; t.gamma = 0.43586652150845899941601945119356;
     t.a[1][0] = 1.0; t.a[2][0] = 1.0;
@@ -385,7 +401,8 @@ std::string emit_mechanism(const MechData& m0, int team, int tpb, bool adjoint, 
     << "\n#define MAXP " << kMaxSide << "\n";
   const RosCoefficients c = ros_coefficients(tableau);
   const std::vector<int> nf = stage_f_reuse(c);
-  o << "#define TABLEAU_ID " << tableau << "\n#define RS " << c.s << "\n#define RORDER " << c.order
+  o << "#define TABLEAU_ID " << tableau << "\n#define ERK " << (c.erk ? 1 : 0) << "\n#define RS " << c.s
+    << "\n#define RORDER " << c.order
     << "\n#define NEED_F0 " << (needs_f0(c) ? 1 : 0) << "\n#define RGAM " << num(c.gamma) << "\n";
   emit_array(o, "double", "rk_a", "[" + std::to_string(c.s * c.s) + "]", c.s * c.s,
              [&](int i) { return num(c.a[i / c.s][i % c.s]); });
@@ -680,7 +697,7 @@ int smem_bytes(const MechData& m, int team, int tpb, int tableau) {
 
 int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = false, int tableau = 0) {
   std::lock_guard<std::mutex> lk(m->mu);
-  if (tableau < 0 || tableau > 3) return fail(CHEM_EARG, "unknown Rosenbrock method %d", tableau);
+  if (tableau < 0 || tableau > 4) return fail(CHEM_EARG, "unknown integration method %d", tableau);
   auto key = std::make_tuple(team, tpb, tableau);
   auto& mods = adjoint ? m->adj_modules : m->modules;
   auto it = mods.find(key);
@@ -820,7 +837,7 @@ int chem_mech_compile_only(const char* spec_path, const chem_build_opts* opts, c
   const bool adj = opts && opts->adjoint;
   if (adj && team == 1) return fail(CHEM_EARG, "the adjoint needs a multi-lane configuration (team >= 32)");
   const int tab = opts ? opts->tableau : 0;
-  if (tab < 0 || tab > 3) return fail(CHEM_EARG, "unknown Rosenbrock method %d", tab);
+  if (tab < 0 || tab > 4) return fail(CHEM_EARG, "unknown integration method %d", tab);
   if (adj && tab != 0) return fail(CHEM_EARG, "the adjoint is implemented for ROS4 (tableau 0)");
   int rc = build_cubin(d, team, tpb, adj, tab, opts ? opts->cache_dir : nullptr, opts && opts->verbose, &cubin, &lg);
   if (log && log_cap) {

@@ -782,6 +782,26 @@ __device__ __forceinline__ void stage_solve(const Team& tm, int ob) {
 template <bool REG_SOLVE = (NB >= 3)>
 __device__ double ros4_attempt(const Team& tm, double P, double hh, double rtol, double atol,
                               const double* lnA_ext) {
+#if ERK
+  // explicit Runge-Kutta (RKF45) in increment form: u_i = hh f(y + sum_{j<i} a_ij u_j); no
+  // Jacobian, no factorisation
+#pragma unroll
+  for (int st = 0; st < RS; ++st) {
+    if (st > 0) {
+      for (int i = tm.tl; i < NEQ; i += TEAM) {
+        double v = tm.at(OFF_Y, i);
+        for (int j = 0; j < st; ++j)
+          if (rk_a[st * RS + j] != 0.0) v += rk_a[st * RS + j] * tm.at(UOFF(j), i);
+        tm.at(OFF_YT, i) = v;
+      }
+      tsync();
+    }
+    eval_f(tm, st == 0 ? OFF_Y : OFF_YT, OFF_F, P, lnA_ext);
+    const int ou = UOFF(st);
+    for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(ou, i) = hh * tm.at(OFF_F, i);
+    tsync();
+  }
+#else
   // stage 1: f0 into U1, M = I/(gamma h) - J
   eval_f_jac(tm, OFF_Y, OFF_U1, P, lnA_ext, -1.0, 1.0 / (RGAM * hh));
 #if NEED_F0
@@ -818,6 +838,7 @@ __device__ double ros4_attempt(const Team& tm, double P, double hh, double rtol,
     tsync();
     stage_solve<REG_SOLVE>(tm, ou);
   }
+#endif
   // new state, error estimate and its weighted RMS norm
   double acc = 0.0;
   bool bad = false;
@@ -874,8 +895,10 @@ __device__ __forceinline__ void ros4_advance(const Team& tm, Ctl& c, double P, d
     const double e = err > 1e-10 ? err : 1e-10;
 #if RORDER == 4
     fac = 0.9 / sqrt(sqrt(e));  // 0.9 err^(-1/order)
-#else
+#elif RORDER == 3
     fac = 0.9 / cbrt(e);
+#else
+    fac = 0.9 * pow(e, -1.0 / RORDER);
 #endif
     fac = fac < 0.2 ? 0.2 : (fac > 6.0 ? 6.0 : fac);
   }

@@ -348,6 +348,46 @@ def test_other_rosenbrock_methods(omech, gmech, name, tab):
     assert weighted_norm(yo, yg)[same].max() <= 1e-5
 
 
+@pytest.mark.parametrize("team,block", [(64, 64), (32, 64), (1, 32)])
+def test_rkf45_parity(omech, gmech, team, block):
+    """The explicit RKF45 of the paper's solver table on the non-stiff H2 cells (1 us split
+    steps) against the oracle running RKF45: same per-cell result for matching step sequences,
+    and it finishes the split step in fewer attempts than ROS4 on these cells."""
+    import torch
+    name = "h2_13"
+    om = omech(name)
+    g = gmech(name, team, block)
+    n = 400
+    st, y0 = _inputs(om, name, n, 141)
+    T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    status = torch.full((n,), -1, dtype=torch.int32, device=T.device)
+    att = torch.zeros(n, dtype=torch.int32, device=T.device)
+    g.integrate(T, P, Y, 1e-6, status=status, opts=g.opts(attempts=att, tableau=4))
+    assert (status.cpu().numpy() == 0).all()
+    yo, info = om.integrate(y0, st.P, 1e-6, threads=16, tableau=4)
+    yg = gpu_state(om, T, Y)
+    same = info["attempts"] == att.cpu().numpy()
+    assert same.mean() >= 0.98
+    assert weighted_norm(yo, yg)[same].max() <= 1e-5
+    _, info4 = om.integrate(y0, st.P, 1e-6, threads=16)
+    assert att.cpu().numpy().mean() < info4["attempts"].mean()
+
+
+def test_rkf45_on_stiff_cells_reports_max_steps(gmech):
+    """On stiff chemistry the explicit method's stable steps are tiny: the cells stop at the
+    attempt limit (a per-cell status, not a fault), their last accepted state finite."""
+    import torch
+    from paper_2205_05681_gb300 import chem
+    g = gmech("ch4_53", 64, 64)
+    st = states("ch4_53", 32, "ch4_partial", 142)
+    T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    status = torch.full((32,), -1, dtype=torch.int32, device=T.device)
+    g.integrate(T, P, Y, 1e-6, status=status, opts=g.opts(tableau=chem.RKF45, max_steps=2000))
+    s = status.cpu().numpy()
+    assert set(s.tolist()) <= {0, 1, 2} and (s != 0).sum() >= 8
+    assert torch.isfinite(T).all() and torch.isfinite(Y).all()
+
+
 def test_interleaved_reaction_order(mech_dir, mech_path):
     """A file with reactions of every kind interleaved: the library runs them in its own
     branch-grouped kernel order and maps run-time ln A, the per-reaction VJP rows and the
