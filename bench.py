@@ -58,7 +58,7 @@ def measured_traffic(wl, full_size):
 
 def algorithmic_flops_per_attempt(spec, tableau=0):
     """FP64 operations of one step attempt by the algorithm's own operation counts
-    (transcendentals exp/log/log10 counted separately, not folded in; see DESIGN.md):
+    (transcendentals exp/log/log10 counted separately, not folded in):
       LU 2N^3/3, s triangular solves 2N^2 each, the Jacobian's dense chain-rule pass 6N^2,
       and per evaluation of f: thermo 27 per species, 4 + 2*(orders) + 2*(species entries) per
       reaction (+2 per efficiency entry and +2 for third-body/falloff reactions, +12 for the
