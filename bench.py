@@ -41,9 +41,9 @@ METHODS = ["ROS4", "ROS3", "RODAS3", "RODAS4", "RKF45"]
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one chem_integrate_k launch on the
 # full bench workload, from a single-pass ncu capture; valid only for the device source they were
 # taken on (sha1 of csrc/ros4_device.cuh), reported as null once that source changes.
-MEASURED_TRAFFIC = {"device_src_sha1": "e0d474acdd2bfe7ddc63a5c3c63de45781257898",
-                    "ch4_53_fwd": 30329600 + 1221376,
-                    "ch4_111_batched": 261532672 + 243226624}
+MEASURED_TRAFFIC = {"device_src_sha1": "bab391c2f4da7a43cc3c456c25b2ad85fc822e0e",
+                    "ch4_53_fwd": 30383104 + 1286656,
+                    "ch4_111_batched": 263212800 + 243468288}
 
 
 def measured_traffic(wl, full_size):

@@ -475,6 +475,25 @@ std::string emit_mechanism(const MechData& m0, int team, int tpb, bool adjoint, 
     for (int i = 0; i < m.rx[r].nre; ++i) d -= m.rx[r].rnu[i];
     return std::to_string(d);
   });
+  // the same coefficients as doubles: the rate arithmetic reads them without an integer-to-FP64
+  // conversion (on GB300 every FP64-pipe instruction is scarce)
+  auto side_table_f = [&](const char* name, int ReactionData::*cnt, int (ReactionData::*arr)[kMaxSide]) {
+    o << "__device__ const double " << name << RP << " = {";
+    for (int r = 0; r < nr; ++r) {
+      o << (r ? "," : "") << "{";
+      for (int i = 0; i < kMaxSide; ++i) o << (i ? "," : "") << (i < m.rx[r].*cnt ? (m.rx[r].*arr)[i] : 0) << ".0";
+      o << "}";
+    }
+    o << "};\n";
+  };
+  side_table_f("mk_rnuf", &ReactionData::nre, &ReactionData::rnu);
+  side_table_f("mk_pnuf", &ReactionData::npr, &ReactionData::pnu);
+  emit_array(o, "double", "mk_dnuf", R, nr, [&](int r) {
+    int d = 0;
+    for (int i = 0; i < m.rx[r].npr; ++i) d += m.rx[r].pnu[i];
+    for (int i = 0; i < m.rx[r].nre; ++i) d -= m.rx[r].rnu[i];
+    return std::to_string(d) + ".0";
+  });
   std::vector<int> off(nr + 1, 0), esp;
   std::vector<double> eval;
   for (int r = 0; r < nr; ++r) {

@@ -361,13 +361,13 @@ __device__ __forceinline__ void reaction_loop(const Team& tm, const CellScalars&
     const double qnet = fwd - rev;
     const double q = m * qnet;
     // shared-memory reductions without a return value do not stall the lane (TEAM > 1)
-    for (int i = 0; i < nre; ++i) scatter_add<double>(&tm.at(OFF_OM, mk_rsp[r][i]), -mk_rnu[r][i] * q);
-    for (int i = 0; i < npr; ++i) scatter_add<double>(&tm.at(OFF_OM, mk_psp[r][i]), mk_pnu[r][i] * q);
+    for (int i = 0; i < nre; ++i) scatter_add<double>(&tm.at(OFF_OM, mk_rsp[r][i]), -mk_rnuf[r][i] * q);
+    for (int i = 0; i < npr; ++i) scatter_add<double>(&tm.at(OFF_OM, mk_psp[r][i]), mk_pnuf[r][i] * q);
     if (WJ) {
       // d ln Kc / dT = (sum nu'' h/RT - sum nu' h/RT - dnu) / T
-      double dlKc = -dnu;
-      for (int i = 0; i < npr; ++i) dlKc += mk_pnu[r][i] * tm.at(OFF_HRT, mk_psp[r][i]);
-      for (int i = 0; i < nre; ++i) dlKc -= mk_rnu[r][i] * tm.at(OFF_HRT, mk_rsp[r][i]);
+      double dlKc = -mk_dnuf[r];
+      for (int i = 0; i < npr; ++i) dlKc += mk_pnuf[r][i] * tm.at(OFF_HRT, mk_psp[r][i]);
+      for (int i = 0; i < nre; ++i) dlKc -= mk_rnuf[r][i] * tm.at(OFF_HRT, mk_rsp[r][i]);
       dlKc *= invT;
       const double dqdT = m * (fwd * dlkf_dT - rev * (dlkf_dT - dlKc));
       // dq/d[M]: the [M] factor of THIRD reactions, the falloff blend of LIND/TROE
@@ -378,7 +378,7 @@ __device__ __forceinline__ void reaction_loop(const Team& tm, const CellScalars&
       int nd = 0;
       for (int i = 0; i < nre; ++i) {
         const int nu = mk_rnu[r][i];
-        double p = m * kf * nu;
+        double p = m * kf * mk_rnuf[r][i];
         for (int i2 = 0; i2 < nre; ++i2) {
           const double c = tm.at(OFF_C, mk_rsp[r][i2]);
           const int e = i2 == i ? nu - 1 : mk_rnu[r][i2];
@@ -389,7 +389,7 @@ __device__ __forceinline__ void reaction_loop(const Team& tm, const CellScalars&
       }
       for (int i = 0; i < npr; ++i) {
         const int nu = mk_pnu[r][i];
-        double p = -m * kr * nu;
+        double p = -m * kr * mk_pnuf[r][i];
         for (int i2 = 0; i2 < npr; ++i2) {
           const double c = tm.at(OFF_C, mk_psp[r][i2]);
           const int e = i2 == i ? nu - 1 : mk_pnu[r][i2];
@@ -402,7 +402,7 @@ __device__ __forceinline__ void reaction_loop(const Team& tm, const CellScalars&
         const int np = side == 0 ? nre : npr;
         for (int i = 0; i < np; ++i) {
           const int k = side == 0 ? mk_rsp[r][i] : mk_psp[r][i];
-          const double nuk = side == 0 ? -mk_rnu[r][i] : mk_pnu[r][i];
+          const double nuk = side == 0 ? -mk_rnuf[r][i] : mk_pnuf[r][i];
           const int row = smap(k);
           for (int d = 0; d < nd; ++d) scatter_add<double>(&tm.A(row, smap(dsp[d])), nuk * dq[d]);
           scatter_add<double>(&tm.at(OFF_DOMT, k), nuk * dqdT);
@@ -1419,18 +1419,18 @@ __device__ void vjp(const Team& tm, double P, const double* __restrict__ lnA_ext
     S kr = kf, fwd = kf, rev = Z + 1.0;
     const int nre = mk_nre[r], npr = mk_npr[r];
     S abar = Z;
-    S dlKc = Z - (double)mk_dnu[r];
+    S dlKc = Z - mk_dnuf[r];
     for (int i = 0; i < nre; ++i) {
       const int sp = mk_rsp[r][i];
       for (int q = 0; q < mk_rnu[r][i]; ++q) { fwd = fwd * sb[VS_C + sp]; kr = kr * sb[VS_EX + sp]; }
-      abar = abar - mk_rnu[r][i] * sb[VS_AT + sp];
-      dlKc = dlKc - mk_rnu[r][i] * sb[VS_HRT + sp];
+      abar = abar - mk_rnuf[r][i] * sb[VS_AT + sp];
+      dlKc = dlKc - mk_rnuf[r][i] * sb[VS_HRT + sp];
     }
     for (int i = 0; i < npr; ++i) {
       const int sp = mk_psp[r][i];
       for (int q = 0; q < mk_pnu[r][i]; ++q) { rev = rev * sb[VS_C + sp]; kr = kr * sb[VS_IEX + sp]; }
-      abar = abar + mk_pnu[r][i] * sb[VS_AT + sp];
-      dlKc = dlKc + mk_pnu[r][i] * sb[VS_HRT + sp];
+      abar = abar + mk_pnuf[r][i] * sb[VS_AT + sp];
+      dlKc = dlKc + mk_pnuf[r][i] * sb[VS_HRT + sp];
     }
     const int dnu = mk_dnu[r];
     for (int q = 0; q < dnu; ++q) kr = kr * rtp;
@@ -1455,7 +1455,7 @@ __device__ void vjp(const Team& tm, double P, const double* __restrict__ lnA_ext
     // d q / d C_j of the mass-action products
     for (int i = 0; i < nre; ++i) {
       const int nu = mk_rnu[r][i];
-      S p = m * kf * (double)nu;
+      S p = m * kf * mk_rnuf[r][i];
       for (int i2 = 0; i2 < nre; ++i2) {
         const int e = i2 == i ? nu - 1 : mk_rnu[r][i2];
         for (int t = 0; t < e; ++t) p = p * sb[VS_C + mk_rsp[r][i2]];
@@ -1464,7 +1464,7 @@ __device__ void vjp(const Team& tm, double P, const double* __restrict__ lnA_ext
     }
     for (int i = 0; i < npr; ++i) {
       const int nu = mk_pnu[r][i];
-      S p = -(m * kr * (double)nu);
+      S p = -(m * kr * mk_pnuf[r][i]);
       for (int i2 = 0; i2 < npr; ++i2) {
         const int e = i2 == i ? nu - 1 : mk_pnu[r][i2];
         for (int t = 0; t < e; ++t) p = p * sb[VS_C + mk_psp[r][i2]];
