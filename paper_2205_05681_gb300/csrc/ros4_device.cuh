@@ -271,6 +271,18 @@ __device__ __forceinline__ void thermo_conc(const Team& tm, int oy, double P, Ce
 
 // ------------------------------------------------------------------------------ reactions
 
+// -x by flipping the sign bit (integer pipe)
+__device__ __forceinline__ double dneg(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+// nu * x for an integer stoichiometric coefficient nu (nuf = nu as a double): no FP64
+// instruction when |nu| = 1, the common case
+__device__ __forceinline__ double nu_times(int nu, double nuf, double x) {
+  if (nu == 1) return x;
+  if (nu == -1) return dneg(x);
+  return nuf * x;
+}
+
 // species index -> row/column of the state matrix: species 0..NS-2 -> 1..NS-1, bath -> 0
 __device__ __forceinline__ int smap(int k) { return k == BATH ? 0 : k + 1; }
 
@@ -361,8 +373,10 @@ __device__ __forceinline__ void reaction_loop(const Team& tm, const CellScalars&
     const double qnet = fwd - rev;
     const double q = m * qnet;
     // shared-memory reductions without a return value do not stall the lane (TEAM > 1)
-    for (int i = 0; i < nre; ++i) scatter_add<double>(&tm.at(OFF_OM, mk_rsp[r][i]), -mk_rnuf[r][i] * q);
-    for (int i = 0; i < npr; ++i) scatter_add<double>(&tm.at(OFF_OM, mk_psp[r][i]), mk_pnuf[r][i] * q);
+    for (int i = 0; i < nre; ++i)
+      scatter_add<double>(&tm.at(OFF_OM, mk_rsp[r][i]), nu_times(-mk_rnu[r][i], -mk_rnuf[r][i], q));
+    for (int i = 0; i < npr; ++i)
+      scatter_add<double>(&tm.at(OFF_OM, mk_psp[r][i]), nu_times(mk_pnu[r][i], mk_pnuf[r][i], q));
     if (WJ) {
       // d ln Kc / dT = (sum nu'' h/RT - sum nu' h/RT - dnu) / T
       double dlKc = -mk_dnuf[r];
@@ -402,14 +416,16 @@ __device__ __forceinline__ void reaction_loop(const Team& tm, const CellScalars&
         const int np = side == 0 ? nre : npr;
         for (int i = 0; i < np; ++i) {
           const int k = side == 0 ? mk_rsp[r][i] : mk_psp[r][i];
+          const int nui = side == 0 ? -mk_rnu[r][i] : mk_pnu[r][i];
           const double nuk = side == 0 ? -mk_rnuf[r][i] : mk_pnuf[r][i];
           const int row = smap(k);
-          for (int d = 0; d < nd; ++d) scatter_add<double>(&tm.A(row, smap(dsp[d])), nuk * dq[d]);
-          scatter_add<double>(&tm.at(OFF_DOMT, k), nuk * dqdT);
+          for (int d = 0; d < nd; ++d) scatter_add<double>(&tm.A(row, smap(dsp[d])), nu_times(nui, nuk, dq[d]));
+          scatter_add<double>(&tm.at(OFF_DOMT, k), nu_times(nui, nuk, dqdT));
           if (kind != ELEM) {
-            scatter_add<double>(&tm.at(OFF_BK, k), nuk * beta);
+            const double nb = nu_times(nui, nuk, beta);
+            scatter_add<double>(&tm.at(OFF_BK, k), nb);
             for (int e = mk_effoff[r]; e < mk_effoff[r + 1]; ++e)
-              scatter_add<double>(&tm.A(row, smap(mk_effsp[e])), nuk * beta * mk_effval[e]);
+              scatter_add<double>(&tm.A(row, smap(mk_effsp[e])), nb * mk_effval[e]);
           }
         }
       }
