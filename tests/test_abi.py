@@ -42,3 +42,23 @@ def test_generated_kernels_compile_for_sm103a(tmp_path):
     log = chem.compile_only(os.path.join(ROOT, "tests", "golden", "tiny_hon7.mech"), team=32,
                             block=64)
     assert "sm_103a" in log and "chem_integrate_k" in log
+
+
+@pytest.mark.parametrize("tableau", [1, 2, 3, 4])
+def test_every_method_compiles(tmp_path, tableau):
+    """ROS3, RODAS3, RODAS4 and the explicit RKF45 generate and compile (NVRTC, no GPU)."""
+    from paper_2205_05681_gb300 import chem
+    log = chem.compile_only(os.path.join(ROOT, "tests", "golden", "tiny_hon7.mech"), team=64,
+                            block=64, cache_dir=str(tmp_path), tableau=tableau)
+    assert "sm_103a" in log and "chem_integrate_k" in log
+
+
+def test_adjoint_module_compiles_and_refuses_other_methods(tmp_path):
+    from paper_2205_05681_gb300 import chem
+    mech = os.path.join(ROOT, "tests", "golden", "tiny_hon7.mech")
+    log = chem.compile_only(mech, team=64, block=64, cache_dir=str(tmp_path), adjoint=True)
+    assert "chem_adjoint_k" in log and "chem_eval_vjp_k" in log
+    with pytest.raises(chem.ChemError, match="adjoint"):
+        chem.compile_only(mech, team=64, block=64, cache_dir=str(tmp_path), adjoint=True, tableau=1)
+    with pytest.raises(chem.ChemError, match="unknown integration method"):
+        chem.compile_only(mech, team=64, block=64, cache_dir=str(tmp_path), tableau=7)
