@@ -100,7 +100,10 @@ typedef struct {
 /* Parse a mechanism spec file (format: paper_2205_05681_gb300/synth.py docstring), build its
  * tables, generate its specialised CUDA source and compile it for sm_103a with NVRTC (or load
  * the cubin from cache_dir).  Host-side; needs a current CUDA device to load the module.
- * out receives the handle.  Errors: CHEM_EIO, CHEM_ENVRTC, CHEM_ECUDA. */
+ * out receives the handle.  Errors: CHEM_EIO, CHEM_ENVRTC, CHEM_ECUDA.
+ * Reaction order: every per-reaction array of this interface (lnA inputs, g_lnA and the VJP's
+ * gp outputs, chem_mech_lnA) is in the file's reaction order; the kernels run the reactions in
+ * their own branch-grouped order internally and map back. */
 int chem_mech_load(const char* spec_path, const chem_build_opts* opts, chem_mech_t* out);
 
 /* As chem_mech_load but only generates and compiles the source (no CUDA device needed); used
