@@ -41,9 +41,9 @@ METHODS = ["ROS4", "ROS3", "RODAS3", "RODAS4", "RKF45"]
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one chem_integrate_k launch on the
 # full bench workload, from a single-pass ncu capture; valid only for the device source they were
 # taken on (sha1 of csrc/ros4_device.cuh), reported as null once that source changes.
-MEASURED_TRAFFIC = {"device_src_sha1": "bab391c2f4da7a43cc3c456c25b2ad85fc822e0e",
-                    "ch4_53_fwd": 30383104 + 1286656,
-                    "ch4_111_batched": 263212800 + 243468288}
+MEASURED_TRAFFIC = {"device_src_sha1": "c6747bf2e79e40569ff2a68abd923dabdb93cf39",
+                    "ch4_53_fwd": 30189056 + 1082112,
+                    "ch4_111_batched": 261837312 + 240503296}
 
 
 def measured_traffic(wl, full_size):
