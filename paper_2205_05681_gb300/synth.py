@@ -583,11 +583,13 @@ def make_states(mech: Mechanism, n_cells: int, recipe: str, seed: int) -> States
     return States(T.astype(np.float64), P.astype(np.float64), Y.astype(np.float64))
 
 
-# the five workloads: (mechanism, cells, recipe, state seed, dt [s], split steps)
+# the workloads: (mechanism, cells, recipe, state seed, dt [s], split steps)
 WORKLOADS = {
     "h2_13_fwd": ("h2_13", 1024, "h2_fresh", 7, 1e-6, 1),
     "ch4_53_fwd": ("ch4_53", 65536, "ch4_partial", 8, 1e-6, 1),
     "ch4_111_batched": ("ch4_111", 262144, "ch4_front", 9, 1e-6, 20),
     "ch4_53_adjoint": ("ch4_53", 16384, "ch4_ign", 10, 1e-4, 1),
     "ch4_111_adjoint": ("ch4_111", 65536, "ch4_ign_wide", 11, 5e-4, 1),
+    # the 13-species cells at a batch that fills the GPU (method comparison at throughput)
+    "h2_13_wide": ("h2_13", 65536, "h2_fresh", 12, 1e-6, 1),
 }
