@@ -276,11 +276,16 @@ __device__ __forceinline__ double dneg(double x) {
   return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
 }
 // nu * x for an integer stoichiometric coefficient nu (nuf = nu as a double): no FP64
-// instruction when |nu| = 1, the common case
+// instruction when |nu| = 1, the common case.  The adjoint module keeps the multiply (its
+// kernels measured faster with it); the results are the same bits either way.
 __device__ __forceinline__ double nu_times(int nu, double nuf, double x) {
+#if defined(CHEM_ADJOINT)
+  return nuf * x;
+#else
   if (nu == 1) return x;
   if (nu == -1) return dneg(x);
   return nuf * x;
+#endif
 }
 
 // species index -> row/column of the state matrix: species 0..NS-2 -> 1..NS-1, bath -> 0
