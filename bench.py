@@ -1,10 +1,20 @@
 """Throughput of the batched ROS4 chemistry integrator on GB300 (one JSON line on stdout).
 
-A step = one operator-split chemistry step of the whole workload: every cell of the batch is
-integrated over dt with adaptive ROS4 (FP64, rtol 1e-6, atol 1e-10) by one persistent-kernel
-call.  The timed workload is the 53-species / 325-reaction synthetic mechanism on 65,536 cells
-(dt = 1e-6 s); inputs are restored to the same initial state before every step and L2 is flushed
-(a 512 MiB write) between steps; each step is timed with CUDA events on the launching stream.
+A step = one pass of the batched hot path over the whole workload.  The default workload is the
+batched flame-front configuration: the 111-species / 784-reaction synthetic mechanism on
+262,144 cells (90% relaxed products, 10% ignition-front cells), 20 consecutive operator-split
+steps of dt = 1e-6 s (h carried from step to step) captured once as a CUDA graph and replayed
+per bench step, adaptive ROS4 in FP64 at rtol 1e-6 / atol 1e-10, in the kernel configuration the
+library's autotuner picks on a sample of the cells (autotune time reported, not timed).  Inputs
+are restored before every step and L2 is flushed (a 512 MiB write); steps are timed with CUDA
+events on the launching stream.  value = cell split-steps per second.
+
+Beside the timed line: the plain one-launch-per-attempt GPU driver on the same inputs, the same
+workload end to end from pinned host arrays through chem_integrate_host, the 53-species forward
+workload (65,536 cells, one split step), the discrete adjoint on the 53-species ignition
+workload and on the 111-species workload under a stated HBM budget, FP64 roofline figures
+against an in-run FMA-chain peak and the cuBLAS float64 GEMM, and the CPU oracle on the host
+cores (a bounded sample).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
@@ -57,40 +67,44 @@ def measured_traffic(wl, full_size):
 
 
 def algorithmic_flops_per_attempt(spec, tableau=0):
-    """FP64 operations of one step attempt by the algorithm's own operation counts
-    (transcendentals exp/log/log10 counted separately, not folded in):
+    """FP64 operations of one step attempt by the algorithm's own operation counts, with the
+    transcendentals counted separately (returned as a dict of exp and log calls):
       LU 2N^3/3, s triangular solves 2N^2 each, the Jacobian's dense chain-rule pass 6N^2,
       and per evaluation of f: thermo 27 per species, 4 + 2*(orders) + 2*(species entries) per
       reaction (+2 per efficiency entry and +2 for third-body/falloff reactions, +12 for the
       falloff blend, +40 for Troe); the Jacobian adds per reaction 2 p^2 + 10 (+2 per efficiency
       entry x participant) for its p participants.  RKF45: six evaluations of f and the stage
-      combinations only.  ROS4 evaluates f at 3 points (stage 4 reuses
-      stage 3's argument)."""
+      combinations only.  ROS4 evaluates f at 3 points (stage 4 reuses stage 3's argument).
+      Transcendentals per evaluation of f: one exp per species (equilibrium factor) and per
+      reaction (forward rate constant), one more per falloff reaction (low-pressure limit), and
+      for Troe reactions three exp (the blending terms, two without T**) plus the final exp and
+      two log10; one log of T."""
     s, nf = METHOD_SHAPE[tableau]
     N = spec["ns"]
     fl = 0.0 if tableau in EXPLICIT else 2.0 * N ** 3 / 3.0 + s * 2.0 * N ** 2 + 6.0 * N ** 2
     f_eval = 27.0 * N
     jac = 0.0
-    trans_f = N + 1  # exp per species + log T
+    n_exp, n_log = N, 1
     for r in spec["reactions"]:
         nre, npr = sum(r["rnu"]), sum(r["pnu"])
         f_eval += 4 + 2 * (nre + npr) + 2 * (len(r["rnu"]) + len(r["pnu"]))
-        trans_f += 1
+        n_exp += 1
         if r["kind"] != "ELEM":
             f_eval += 2 * r["neff"] + 2
         if r["kind"] in ("LIND", "TROE"):
             f_eval += 12
-            trans_f += 1
+            n_exp += 1
         if r["kind"] == "TROE":
             f_eval += 40
-            trans_f += 6
+            n_exp += 3 + (1 if r.get("t2", 0.0) > 0.0 else 0)
+            n_log += 2
         p = len(r["rnu"]) + len(r["pnu"])
         jac += 2 * p * p + 10 + (2 * r["neff"] * p if r["kind"] != "ELEM" else 0)
     if tableau in EXPLICIT:
         jac = 0.0
         fl += 2.0 * s * N  # the stage combinations
     total = fl + nf * f_eval + jac
-    return total, nf * trans_f
+    return total, {"exp": nf * n_exp, "log": nf * n_log}
 
 
 def read_spec_counts(path):
@@ -109,6 +123,8 @@ def read_spec_counts(path):
             rx.append({"kind": t[1], "rnu": rnu, "pnu": pnu, "neff": 0})
         elif t[0] == "EFF":
             rx[-1]["neff"] = int(t[1])
+        elif t[0] == "TROE":
+            rx[-1]["t2"] = float(t[4])
     return {"ns": ns, "reactions": rx}
 
 
@@ -226,9 +242,10 @@ def cpu_oracle_rate(path, wl, budget_s=15.0, max_cells=4096, tableau=0, rtol=1e-
         el = time.perf_counter() - t0
         if el >= min(2.0, budget_s) or reps >= 1000:
             break
-    return reps * ns * splits / el, cores, (
-        "%d of %d cells (evenly strided) x %d split steps%s, %.1f s on %d host threads" % (
-            ns, n_cells, splits, "" if reps == 1 else " x %d repeats" % reps, el, cores))
+    return {"value": reps * ns * splits / el, "cores": cores, "seconds": el, "cells": ns,
+            "repeats": reps,
+            "sample": "%d of %d cells (evenly strided) x %d split steps%s, %.1f s on %d host threads" % (
+                ns, n_cells, splits, "" if reps == 1 else " x %d repeats" % reps, el, cores)}
 
 
 def relax_products(m, st, T0, P, Y0, torch, np, n_templates=1024, t_relax=1e-3):
@@ -259,12 +276,12 @@ def relax_products(m, st, T0, P, Y0, torch, np, n_templates=1024, t_relax=1e-3):
             "front_cells": int(front.sum()), "product_cells": int(len(idx))}
 
 
-def adjoint_leg(chem, synth, torch, np, dev, path53, wl="ch4_53_adjoint", cells=0, cap=4096,
-                interval=16):
-    """Checkpointed forward + discrete adjoint on an ignition workload (default: 53 species,
-    16,384 cells, 1e-4 s): loss = sum (T - T_target)^2 with T_target from a seeded ln A
-    perturbation + noise; times the taped forward, the plain forward and the reverse sweep (CUDA
-    events)."""
+def adjoint_leg(chem, synth, torch, np, dev, wl="ch4_53_adjoint", cells=0, cap=4096,
+                interval=16, hbm_budget_gib=None):
+    """Checkpointed forward + discrete adjoint on an adjoint workload: loss = sum (T - T_target)^2
+    with T_target from a seeded ln A perturbation + noise; times the taped forward, the untaped
+    forward and the reverse sweep (CUDA events), after an untimed call on a few cells that loads
+    the adjoint module.  Reports the tape and adjoint-workspace bytes against hbm_budget_gib."""
     mech_name, n, recipe, seed, dt, _ = synth.WORKLOADS[wl]
     if cells:
         n = min(n, cells)
@@ -280,41 +297,59 @@ def adjoint_leg(chem, synth, torch, np, dev, path53, wl="ch4_53_adjoint", cells=
     Tt, Yt = T0.clone(), Y0.clone()
     m.integrate(Tt, P, Yt, dt, opts=m.opts(lnA=lnA_t))
     T_target = Tt + torch.tensor(rng.normal(0.0, 1.0, n), device=dev)
+    # untimed: compile and load the adjoint module on a few cells
+    k = min(n, 4)
+    tw = m.make_tape(k, cap, interval, device=dev)
+    Tw, Yw = T0[:k].clone(), Y0[:, :k].contiguous()
+    m.integrate_ckpt(Tw, P[:k].contiguous(), Yw, dt * 1e-3, tw)
+    m.adjoint(P[:k].contiguous(), torch.ones_like(Tw), torch.zeros_like(Yw), tw)
+    del tw
     tape = m.make_tape(n, cap, interval, device=dev)
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     status = torch.empty(n, dtype=torch.int32, device=dev)
-    res = {}
-    for rep in range(2):
-        T, Y = T0.clone(), Y0.clone()
-        torch.cuda.synchronize()
-        e0, e1 = ev()
-        e0.record()
-        m.integrate_ckpt(T, P, Y, dt, tape, status=status, opts=m.opts(lnA=lnA))
-        e1.record()
-        e1.synchronize()
-        t_fwd = e0.elapsed_time(e1)
-        gT = 2.0 * (T - T_target)
-        gY = torch.zeros_like(Y)
-        e0, e1 = ev()
-        e0.record()
-        g_lnA, gT0, gY0 = m.adjoint(P, gT, gY, tape, opts=m.opts(lnA=lnA))
-        e1.record()
-        e1.synchronize()
-        t_adj = e0.elapsed_time(e1)
-        T2, Y2 = T0.clone(), Y0.clone()
-        e0, e1 = ev()
-        e0.record()
-        m.integrate(T2, P, Y2, dt, opts=m.opts(lnA=lnA))
-        e1.record()
-        e1.synchronize()
-        t_plain = e0.elapsed_time(e1)
-        res = {"workload": wl, "cells": n, "dt_s": dt, "interval": interval, "capacity": cap,
-               "fwd_ckpt_ms": t_fwd, "fwd_ms": t_plain, "adjoint_ms": t_adj,
-               "adjoint_over_fwd": t_adj / t_plain, "tape_bytes": int(tape.buf.numel()),
-               "accepted_mean": float(tape.n_accepted().float().mean().item()),
-               "ok_cells": int((status == 0).sum().item()),
-               "loss": float(((T - T_target) ** 2).sum().item()),
-               "grad_lnA_norm": float(g_lnA.norm().item())}
+    T, Y = T0.clone(), Y0.clone()
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(dev)
+    base = torch.cuda.memory_allocated(dev)
+    e0, e1 = ev()
+    e0.record()
+    m.integrate_ckpt(T, P, Y, dt, tape, status=status, opts=m.opts(lnA=lnA))
+    e1.record()
+    e1.synchronize()
+    t_fwd = e0.elapsed_time(e1)
+    gT = 2.0 * (T - T_target)
+    gY = torch.zeros_like(Y)
+    ws_bytes = int(m._lib.chem_adjoint_workspace(m._h, n, chem.C.byref(m.opts(lnA=lnA)), interval))
+    e0, e1 = ev()
+    e0.record()
+    g_lnA, gT0, gY0 = m.adjoint(P, gT, gY, tape, opts=m.opts(lnA=lnA))
+    e1.record()
+    e1.synchronize()
+    t_adj = e0.elapsed_time(e1)
+    peak = torch.cuda.max_memory_allocated(dev) - base
+    T2, Y2 = T0.clone(), Y0.clone()
+    e0, e1 = ev()
+    e0.record()
+    m.integrate(T2, P, Y2, dt, opts=m.opts(lnA=lnA))
+    e1.record()
+    e1.synchronize()
+    t_plain = e0.elapsed_time(e1)
+    nacc = tape.n_accepted().float()
+    res = {"workload": wl, "mechanism": mech_name, "cells": n, "dt_s": dt, "interval": interval,
+           "capacity": cap, "fwd_ckpt_ms": t_fwd, "fwd_ms": t_plain, "adjoint_ms": t_adj,
+           "adjoint_over_fwd": t_adj / t_plain, "tape_bytes": int(tape.buf.numel()),
+           "adjoint_workspace_bytes": ws_bytes,
+           "peak_bytes_during_sweep": int(peak),
+           "accepted_mean": float(nacc.mean().item()), "accepted_max": int(nacc.max().item()),
+           "ok_cells": int((status == 0).sum().item()),
+           "loss": float(((T - T_target) ** 2).sum().item()),
+           "grad_lnA_norm": float(g_lnA.norm().item()),
+           "temperature_rise_K": {"p50": float((T - T0).median().item()),
+                                  "max": float((T - T0).max().item())}}
+    if hbm_budget_gib is not None:
+        need = res["tape_bytes"] + ws_bytes
+        res["hbm_budget_bytes"] = int(hbm_budget_gib * 2 ** 30)
+        res["within_budget"] = bool(need <= res["hbm_budget_bytes"])
     return res
 
 
@@ -341,7 +376,25 @@ def dist_env():
     return rank, world, local
 
 
+def workload_config(wl, args, world):
+    """The `config` dict of a workload, identical on the GPU arm and the reference arm."""
+    from paper_2205_05681_gb300 import synth
+    mech_name, n_cells, recipe, seed, dt, splits = synth.WORKLOADS[wl]
+    spec = read_spec_counts(synth.mechanism_file(mech_name, MECH_DIR))
+    if args.cells:
+        n_cells = min(n_cells, args.cells)
+    return {"workload": wl, "mechanism": mech_name, "species": spec["ns"],
+            "reactions": len(spec["reactions"]), "cells": n_cells, "recipe": recipe,
+            "state_seed": seed, "dt_s": dt, "split_steps_per_step": splits,
+            "method": METHODS[args.tableau], "cuda_graph": splits > 1, "rtol": args.rtol,
+            "atol": args.atol, "l2": "flushed (512 MiB write) between steps",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on the host cores; each step integrates a
+    bounded, evenly strided sample of the workload's cells (sized to ~60 s / steps of CPU work)
+    and the step's value is the sample's cells x split steps per second."""
     rank, world, local = dist_env()
     if rank != 0:
         return 0
@@ -351,25 +404,25 @@ def run_reference(args):
     wl = args.workload
     mech_name, n_cells, recipe, seed, dt, splits = synth.WORKLOADS[wl]
     path = synth.mechanism_file(mech_name, MECH_DIR)
-    vals = []
+    runs = []
     kw = dict(tableau=args.tableau, rtol=args.rtol, atol=args.atol)
     for _ in range(args.warmup):
         cpu_oracle_rate(path, wl, budget_s=3.0, **kw)
     for _ in range(args.steps):
-        v, cores, sample = cpu_oracle_rate(path, wl, budget_s=max(3.0, 60.0 / max(args.steps, 1)),
-                                           **kw)
-        vals.append(v)
+        runs.append(cpu_oracle_rate(path, wl, budget_s=max(3.0, 60.0 / max(args.steps, 1)), **kw))
+    vals = [r["value"] for r in runs]
     v = statistics.median(vals)
+    r0 = runs[len(runs) // 2]
+    cfg = workload_config(wl, args, world)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cells/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": n_cells * splits / v * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl, "mechanism": mech_name, "cells": n_cells, "dt_s": dt,
-                       "split_steps_per_step": splits,
-                       "method": METHODS[args.tableau],
-                       "rtol": args.rtol, "atol": args.atol},
-            "cpu_baseline": {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+            # the measured time of one step: the sample that step integrated
+            "ms_per_step": statistics.median(r["seconds"] for r in runs) * 1e3,
+            "ms_per_step_extrapolated_to_workload": cfg["cells"] * splits / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": "cells/s", "cores": r0["cores"],
+                             "kind": "oracle", "sample": r0["sample"]},
             "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -437,22 +490,174 @@ def work_precision(args, chem, synth, torch, np, dev):
             "work_precision": rows}
 
 
+DEFAULT_WORKLOAD = "ch4_111_batched"
+
+
+def prepare_inputs(m, synth, torch, np, dev, wl, cells=0):
+    """Device copies of the workload's seeded states (T0, P, Y0 [Ns, C]); for the flame-front
+    workload the product cells are first relaxed (untimed)."""
+    mech_name, n_cells, recipe, seed, dt, splits = synth.WORKLOADS[wl]
+    st = synth.make_states(synth.mechanism(mech_name), n_cells, recipe, seed)
+    if cells:
+        n_cells = min(n_cells, cells)
+        st = synth.States(st.T[:n_cells], st.P[:n_cells], st.Y[:n_cells])
+    T0 = torch.tensor(st.T, device=dev)
+    P = torch.tensor(st.P, device=dev)
+    Y0 = torch.tensor(np.ascontiguousarray(st.Y.T), device=dev)
+    prep = {}
+    if recipe == "ch4_front":
+        prep = relax_products(m, st, T0, P, Y0, torch, np)
+    return T0, P, Y0, prep
+
+
+def forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, steps, warmup, rtol, atol,
+                tableau=0, clocks_index=None, world=1, plain=True, plain_runs=1):
+    """Times `steps` bench steps (each: restore inputs, flush L2, `splits` split steps, graph-
+    captured when splits > 1) after `warmup` untimed ones; optionally the plain driver on the
+    same inputs.  Returns a dict of times (s), attempts per cell and the clock summary."""
+    n_cells = T0.shape[0]
+    T, Y = T0.clone(), Y0.clone()
+    h = torch.zeros(n_cells, dtype=torch.float64, device=dev)
+    status = torch.zeros(n_cells, dtype=torch.int32, device=dev)
+    att = torch.zeros(n_cells, dtype=torch.int32, device=dev)
+    att_total = torch.zeros(n_cells, dtype=torch.int32, device=dev)
+    opts = m.opts(attempts=att, tableau=tableau)
+    ws = m.workspace(n_cells, opts, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def restore():
+        T.copy_(T0)
+        Y.copy_(Y0)
+        h.zero_()
+        flush.fill_(1.0)  # evict the inputs from L2 (512 MiB > 129 MB)
+
+    def one_split(o=opts, w=ws):
+        m.integrate(T, P, Y, dt, rtol=rtol, atol=atol, h=h, status=status, opts=o, workspace=w)
+
+    if splits > 1:
+        # consecutive split steps (h carried) captured once as a CUDA graph and replayed
+        def splits_body():
+            att_total.zero_()
+            for _ in range(splits):
+                one_split()
+                att_total.add_(att)
+
+        restore()
+        s_cap = torch.cuda.Stream()
+        s_cap.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s_cap):
+            splits_body()  # eager run on the capture stream before capture
+        torch.cuda.current_stream().wait_stream(s_cap)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            splits_body()
+
+        def one_step():
+            graph.replay()
+    else:
+        def one_step():
+            one_split()
+            att_total.copy_(att)
+
+    for _ in range(warmup):
+        restore()
+        one_step()
+    torch.cuda.synchronize()
+    times = []
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(clocks_index if clocks_index is not None else 0) as clk:
+        for _ in range(steps):
+            restore()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    res = {"times": times, "attempts": att_total.cpu().numpy(),
+           "ok_cells": int((status == 0).sum().item()), "clocks": clk.summary()}
+    if plain:
+        # the plain one-launch-per-attempt driver on the same inputs (split steps run eagerly: its
+        # host polling cannot be captured in a graph); one run, its kernels are already loaded
+        po = m.opts(mode=chem.MODE_PLAIN, tableau=tableau)
+        pws = m.workspace(n_cells, po, device=dev)
+        pt = []
+        for _ in range(plain_runs):
+            restore()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(splits):
+                one_split(po, pws)
+            e1.record(stream)
+            e1.synchronize()
+            pt.append(e0.elapsed_time(e1) * 1e-3)
+        res["plain_s"] = min(pt)
+        del pws
+    del ws, flush
+    return res
+
+
+def roofline(spec, tableau, total_attempts, sec, probe, dgemm, sm_mhz, n_sm, wl, full_size,
+             n_cells, launches):
+    """FP64-ALU roofline of chem_integrate_k over the timed region."""
+    fl, trans = algorithmic_flops_per_attempt(spec, tableau)
+    achieved = fl * total_attempts / sec / 1e12
+    folded = (fl + 2.0 * (trans["exp"] * probe["exp_cost"] + trans["log"] * probe["log_cost"]))
+    achieved_t = folded * total_attempts / sec / 1e12
+    peak = probe["dfma_tflops"]
+    N = spec["ns"]
+    traffic = measured_traffic(wl, full_size and tableau == 0)
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "peak_source": "FMA-chain probe (chem_fp64_probe) on this GPU in this run",
+            "peak_dgemm": dgemm, "frac_vs_dgemm": achieved / dgemm,
+            "peak_derived_from_clock": (n_sm * 4.0 * sm_mhz * 1e6 / 1e12) if sm_mhz else None,
+            "peak_derived_note": "SMs x 2 FP64 lanes per clock x 2 flops x median SM clock",
+            "achieved_with_transcendentals": achieved_t,
+            "frac_with_transcendentals": achieved_t / peak,
+            "transcendental_cost_fma": {"exp": probe["exp_cost"], "log": probe["log_cost"]},
+            "traffic": traffic,
+            "traffic_source": ("ncu single-pass capture summarised in profiles/, device-source "
+                               "hash matched" if traffic is not None else None),
+            "traffic_unit": "bytes per launch (one split step)",
+            "algorithmic_bytes_per_launch": int(8 * n_cells * (2 * (N + 1) + 3)),
+            "kernel": "chem_integrate_k", "launches": launches,
+            "flops_per_attempt": fl, "transcendentals_per_attempt": trans}
+
+
+def attempts_summary(a, ok):
+    return {"total": int(a.sum()), "mean": float(a.mean()), "p50": float(np.percentile(a, 50)),
+            "p99": float(np.percentile(a, 99)), "max": int(a.max()),
+            "max_over_p50": float(a.max() / max(np.percentile(a, 50), 1)), "ok_cells": ok}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
-    ap.add_argument("--workload", default="ch4_53_fwd")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--team", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-kernel comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 53-species forward and the two adjoint legs")
     ap.add_argument("--cells", type=int, default=0,
                     help="use only the first CELLS cells of the workload (small profiling runs)")
-    ap.add_argument("--autotune", action="store_true", help="pick (team, block) on a sample first")
-    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward leg")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the library's default kernel configuration instead of autotuning")
     ap.add_argument("--tape-capacity", type=int, default=4096, help="adjoint workloads: steps/cell")
     ap.add_argument("--interval", type=int, default=16, help="adjoint workloads: checkpoint interval")
     ap.add_argument("--tableau", type=int, default=0,
@@ -480,7 +685,7 @@ def main():
             print(json.dumps(work_precision(args, chem, synth, torch, np, dev)), flush=True)
         return 0
     if wl.endswith("_adjoint"):
-        res = adjoint_leg(chem, synth, torch, np, dev, None, wl=wl, cells=args.cells,
+        res = adjoint_leg(chem, synth, torch, np, dev, wl=wl, cells=args.cells,
                           cap=args.tape_capacity, interval=args.interval)
         if rank == 0:
             line = {"metric": "adjoint/forward time (discrete adjoint, ROS4, FP64)",
@@ -489,97 +694,27 @@ def main():
                     "config": {"workload": wl}, "adjoint": res}
             print(json.dumps(line), flush=True)
         return 0
-    mech_name, n_cells, recipe, seed, dt, splits = synth.WORKLOADS[wl]
+    mech_name, n_all, recipe, seed, dt, splits = synth.WORKLOADS[wl]
     path = synth.mechanism_file(mech_name, MECH_DIR + ("" if world == 1 else "_r%d" % rank))
     t0 = time.perf_counter()
     m = chem.Mechanism(path, team=args.team, block=args.block)
     load_s = time.perf_counter() - t0
-    st = synth.make_states(synth.mechanism(mech_name), n_cells, recipe, seed)
-    if args.cells:
-        n_cells = min(n_cells, args.cells)
-        st = synth.States(st.T[:n_cells], st.P[:n_cells], st.Y[:n_cells])
-    T0 = torch.tensor(st.T, device=dev)
-    P = torch.tensor(st.P, device=dev)
-    Y0 = torch.tensor(np.ascontiguousarray(st.Y.T), device=dev)
-    prep = {}
-    if recipe == "ch4_front":
-        prep = relax_products(m, st, T0, P, Y0, torch, np)
-    T, Y = T0.clone(), Y0.clone()
-    h = torch.zeros(n_cells, dtype=torch.float64, device=dev)
-    status = torch.zeros(n_cells, dtype=torch.int32, device=dev)
-    att = torch.zeros(n_cells, dtype=torch.int32, device=dev)
-    opts = m.opts(attempts=att, tableau=args.tableau)
-    ws = m.workspace(n_cells, opts, device=dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-
-    def restore():
-        T.copy_(T0)
-        Y.copy_(Y0)
-        h.zero_()
-        flush.fill_(1.0)  # evict the inputs from L2 (512 MiB > 129 MB)
+    T0, P, Y0, prep = prepare_inputs(m, synth, torch, np, dev, wl, args.cells)
+    n_cells = T0.shape[0]
 
     tuned = None
-    if args.autotune:
+    if not args.no_autotune and not args.team:
+        t0 = time.perf_counter()
         tuned = m.autotune(T0, P, Y0, dt)
-        opts = m.opts(attempts=att, tableau=args.tableau)
-    att_total = torch.zeros(n_cells, dtype=torch.int32, device=dev)
+        tuned["autotune_wall_s"] = time.perf_counter() - t0
+        tuned["sample_cells"] = min(n_cells, 4096)
 
-    def one_split(o=opts, w=ws):
-        m.integrate(T, P, Y, dt, rtol=args.rtol, atol=args.atol, h=h, status=status, opts=o,
-                    workspace=w)
-
-    graph = None
-    if splits > 1:
-        # consecutive split steps (h carried) captured once as a CUDA graph and replayed
-        def splits_body():
-            att_total.zero_()
-            for _ in range(splits):
-                one_split()
-                att_total.add_(att)
-
-        restore()
-        s_cap = torch.cuda.Stream()
-        s_cap.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(s_cap):
-            splits_body()  # eager run on the capture stream before capture
-        torch.cuda.current_stream().wait_stream(s_cap)
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            splits_body()
-
-        def one_step(o=opts, w=ws):
-            graph.replay()
-    else:
-        def one_step(o=opts, w=ws):
-            one_split(o, w)
-            att_total.copy_(att)
-
-    for _ in range(args.warmup):
-        restore()
-        one_step()
-    torch.cuda.synchronize()
-    times = []
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        for _ in range(args.steps):
-            restore()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            one_step()
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1) * 1e-3)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    sec = reduce_max_seconds(sum(times) / len(times), world, dev)
+    run = forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, args.steps, args.warmup,
+                      args.rtol, args.atol, tableau=args.tableau, clocks_index=local,
+                      world=world, plain=not args.no_plain)
+    sec = reduce_max_seconds(sum(run["times"]) / len(run["times"]), world, dev)
     value = whole_job_value(n_cells, splits, world, sec)
-    attempts = att_total.cpu().numpy()
-    st_ok = int((status.cpu().numpy() == 0).sum())
+    attempts = run["attempts"]
 
     # end to end: pinned host arrays through chem_integrate_host (H2D copies of T, P, Y, h, the
     # integration and D2H copies of T, Y, h, status inside the timed region; one host call per
@@ -608,32 +743,32 @@ def main():
             e2e_t.append(el)
     e2e_sec = statistics.median(e2e_t) if e2e_t else float("nan")
 
-    # plain one-launch-per-attempt kernel on the same inputs
-    plain = None
-    if not args.no_plain:
-        # the plain one-launch-per-attempt driver on the same inputs (split steps run eagerly:
-        # its host polling cannot be captured in a graph)
-        po = m.opts(mode=chem.MODE_PLAIN, tableau=args.tableau)
-        pws = m.workspace(n_cells, po, device=dev)
-        pt = []
-        for i in range(2):
-            restore()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(splits):
-                one_split(po, pws)
-            e1.record(stream)
-            e1.synchronize()
-            if i:
-                pt.append(e0.elapsed_time(e1) * 1e-3)
-        plain = {"value": n_cells * splits / pt[0], "unit": "cells/s", "ms_per_step": pt[0] * 1e3,
-                 "speedup_of_persistent": pt[0] / sec}
-        del pws
-
-    adjoint = None
-    if not args.no_adjoint and splits == 1 and wl == "ch4_53_fwd" and not args.cells:
-        adjoint = adjoint_leg(chem, synth, torch, np, dev, m.spec_path if hasattr(m, "spec_path") else path)
+    extra = {}
+    full = not args.cells and world == 1
+    if full and not args.no_extra and wl == DEFAULT_WORKLOAD and args.tableau == 0:
+        # the 53-species forward workload (one split step over 65,536 cells)
+        wl2 = "ch4_53_fwd"
+        mn2, _, _, _, dt2, sp2 = synth.WORKLOADS[wl2]
+        m2 = chem.Mechanism(synth.mechanism_file(mn2, MECH_DIR))
+        a0, p2, b0, _ = prepare_inputs(m2, synth, torch, np, dev, wl2)
+        r2 = forward_run(m2, chem, torch, np, dev, a0, p2, b0, dt2, sp2, 3, 1, args.rtol,
+                         args.atol, clocks_index=local)
+        s2 = statistics.median(r2["times"])
+        extra["forward_53"] = {"workload": wl2, "cells": a0.shape[0], "value": a0.shape[0] / s2,
+                               "unit": "cells/s", "ms_per_step": s2 * 1e3,
+                               "plain_value": a0.shape[0] / r2["plain_s"],
+                               "speedup_over_plain": r2["plain_s"] / s2,
+                               "kernel": m2.kernel_config(),
+                               "attempts": attempts_summary(r2["attempts"], r2["ok_cells"]),
+                               "_spec": read_spec_counts(m2.spec_path), "_sec": s2}
+        del a0, p2, b0, m2
+        torch.cuda.empty_cache()
+        extra["adjoint"] = adjoint_leg(chem, synth, torch, np, dev, wl="ch4_53_adjoint",
+                                       cap=args.tape_capacity, interval=args.interval)
+        torch.cuda.empty_cache()
+        extra["adjoint_111"] = adjoint_leg(chem, synth, torch, np, dev, wl="ch4_111_adjoint",
+                                           cap=1024, interval=args.interval, hbm_budget_gib=64)
+        torch.cuda.empty_cache()
 
     if rank != 0:
         if world > 1:
@@ -641,45 +776,42 @@ def main():
         return 0
 
     spec = read_spec_counts(path)
-    fl, trans = algorithmic_flops_per_attempt(spec, args.tableau)
-    total_att = float(attempts.sum())
-    achieved = fl * total_att / sec / 1e12
-    peak = fp64_peak_tflops(torch, dev)
-    cfg = m.kernel_config(opts)
+    probe = chem.fp64_probe()
+    dgemm = fp64_peak_tflops(torch, dev)
+    props = torch.cuda.get_device_properties(dev)
+    clk = run["clocks"]
+    rl = roofline(spec, args.tableau, float(attempts.sum()), sec, probe, dgemm, clk.get("sm_mhz"),
+                  props.multi_processor_count, wl, full, n_cells, splits)
+    if "forward_53" in extra:
+        f53 = extra["forward_53"]
+        r53 = roofline(f53.pop("_spec"), 0, float(f53["attempts"]["total"]), f53.pop("_sec"),
+                       probe, dgemm, clk.get("sm_mhz"), props.multi_processor_count, "ch4_53_fwd",
+                       True, f53["cells"], 1)
+        f53["roofline"] = {k: r53[k] for k in ("achieved", "peak", "frac", "frac_vs_dgemm",
+                                                "frac_with_transcendentals", "traffic",
+                                                "traffic_source")}
     cpu = None
     if not args.no_cpu:
         from oracle import oracle as O
         O.build()
-        v, cores, sample = cpu_oracle_rate(path, wl, tableau=args.tableau, rtol=args.rtol,
-                                           atol=args.atol)
-        cpu = {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": sample}
+        r = cpu_oracle_rate(path, wl, tableau=args.tableau, rtol=args.rtol, atol=args.atol)
+        cpu = {"value": r["value"], "unit": "cells/s", "cores": r["cores"], "kind": "oracle",
+               "sample": r["sample"]}
     N = spec["ns"]
+    cfg = workload_config(wl, args, world)
+    kcfg = m.kernel_config(m.opts(tableau=args.tableau))
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl, "mechanism": mech_name, "species": N,
-                   "reactions": len(spec["reactions"]), "cells": n_cells, "dt_s": dt,
-                   "split_steps_per_step": splits,
-                   "method": METHODS[args.tableau],
-                   "cuda_graph": splits > 1,
-                   "rtol": args.rtol, "atol": args.atol, "l2": "flushed (512 MiB write) between steps",
-                   "team": cfg["team"], "block": cfg["block"], "smem_bytes": cfg["smem"],
-                   "regs": cfg["regs"], "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": measured_traffic(wl, not args.cells and args.tableau == 0),
-                     "traffic_unit": "bytes per launch (one split step)",
-                     "algorithmic_bytes_per_launch": int(8 * n_cells * (2 * (N + 1) + 3)),
-                     "kernel": "chem_integrate_k",
-                     "peak_source": "measured float64 GEMM (cuBLAS) on this GPU in this run",
-                     "flops_per_attempt": fl, "transcendentals_per_attempt": trans},
-        "attempts": {"total": int(total_att), "mean": float(attempts.mean()),
-                     "p50": float(np.percentile(attempts, 50)),
-                     "p99": float(np.percentile(attempts, 99)), "max": int(attempts.max()),
-                     "ok_cells": st_ok},
-        "plain_gpu": plain,
-        "adjoint": adjoint,
+        "config": cfg,
+        "kernel": {"team": kcfg["team"], "block": kcfg["block"], "smem_bytes": kcfg["smem"],
+                   "regs": kcfg["regs"], "autotuned": tuned is not None},
+        "roofline": rl,
+        "attempts": attempts_summary(attempts, run["ok_cells"]),
+        "plain_gpu": None if "plain_s" not in run else {
+            "value": n_cells * splits / run["plain_s"], "unit": "cells/s",
+            "ms_per_step": run["plain_s"] * 1e3, "speedup_of_persistent": run["plain_s"] / sec},
         "autotuned": tuned,
         "input_prep": prep or None,
         "e2e": None if not e2e_t else {
@@ -689,9 +821,10 @@ def main():
             "host_memory": "pinned", "host_calls_per_step": splits},
         "cpu_baseline": cpu,
         "gpu_launches": args.steps * splits,
-        "clocks": clk.summary(),
+        "clocks": clk,
         "mech_load_s": load_s,
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -180,8 +180,11 @@ typedef struct {
  * ((capacity-1)/interval + 1) checkpoint states of Ns doubles. */
 size_t chem_tape_bytes(chem_mech_t mech, int64_t n_cells, int32_t capacity, int32_t interval);
 
-/* chem_integrate (persistent driver) that also records the tape.  A cell that accepts more
- * than `capacity` steps stops with status CHEM_STATUS_TAPE_FULL.  workspace: >= 256 bytes. */
+/* chem_integrate (persistent driver) that also records the tape.  A cell whose tape is full
+ * (`capacity` accepted steps recorded) before it reaches dt stops there with status
+ * CHEM_STATUS_TAPE_FULL: its returned T, Y are the state after exactly the recorded steps, so a
+ * reverse sweep over that tape differentiates the returned state, but it has not reached dt.
+ * workspace: >= 256 bytes. */
 #define CHEM_STATUS_TAPE_FULL 5
 int chem_integrate_ckpt(chem_mech_t mech, int64_t n_cells, double* T, const double* P, double* Y,
                         int64_t ld, double dt, double rtol, double atol, double* h,
@@ -253,6 +256,14 @@ int chem_autotune(chem_mech_t mech, int64_t n_cells, const double* T, const doub
  * dynamic shared memory bytes, registers per thread); for reports. */
 int chem_kernel_config(chem_mech_t mech, const chem_int_opts* opts, int32_t* team,
                        int32_t* block, int32_t* smem_bytes, int32_t* regs);
+
+/* Measurement aid: throughput of this GPU's FP64 pipe, measured on `stream` (current context, or
+ * device 0's primary context) with kernels compiled on the spot: dfma_tflops = FLOP/s of
+ * independent FMA chains (2 flops per FMA) in TFLOP/s; exp_cost and log_cost = pipe time of one
+ * double-precision exp and one log, in FMAs (log's includes one add of its argument).  Host-side,
+ * synchronises `stream`, allocates and frees a small device buffer.  Outputs are nullable.
+ * (No counterpart in the paper: it gives the integrator's FP64 roofline its denominator.) */
+int chem_fp64_probe(void* stream, double* dfma_tflops, double* exp_cost, double* log_cost);
 
 /* Message of the last failed call on this thread. */
 const char* chem_last_error(void);

@@ -24,7 +24,7 @@ EXPORTS = ["chem_mech_load", "chem_mech_compile_only", "chem_mech_free", "chem_m
            "chem_mech_lnA", "chem_eval_source", "chem_eval_jacobian", "chem_integrate_workspace",
            "chem_integrate", "chem_integrate_host", "chem_kernel_config", "chem_autotune",
            "chem_tape_bytes", "chem_integrate_ckpt", "chem_adjoint_workspace", "chem_adjoint",
-           "chem_eval_vjp", "chem_adjoint_noalloc", "chem_last_error"]
+           "chem_eval_vjp", "chem_adjoint_noalloc", "chem_fp64_probe", "chem_last_error"]
 STATUS_TAPE_FULL = 5
 
 CACHE_DIR = os.environ.get("CHEM_CACHE_DIR", os.path.join(os.path.dirname(__file__), "_cache"))
@@ -94,6 +94,7 @@ def library(build_if_missing: bool = True):
             lib.chem_eval_vjp.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, i64, vp, vp]
             lib.chem_adjoint_noalloc.argtypes = [vp, i64, vp, vp, vp, i64, C.POINTER(TapeStruct),
                                                  C.POINTER(IntOpts), vp, vp, vp, vp]
+            lib.chem_fp64_probe.argtypes = [vp] + [C.POINTER(C.c_double)] * 3
             lib.chem_autotune.argtypes = [vp, i64, vp, vp, vp, i64, dbl, dbl, dbl, vp,
                                           C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                           C.POINTER(C.c_float)]
@@ -337,6 +338,15 @@ class Mechanism:
         return {"team": t.value, "block": b.value, "smem": s.value, "regs": r.value}
 
 
+def fp64_probe(stream=None):
+    """FP64 pipe throughput of the current GPU: {"dfma_tflops", "exp_cost", "log_cost"} (the
+    last two in FMA-equivalents of pipe time), from chem_fp64_probe."""
+    lib = library()
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(lib.chem_fp64_probe(_stream(stream), C.byref(a), C.byref(b), C.byref(c)))
+    return {"dfma_tflops": a.value, "exp_cost": b.value, "log_cost": c.value}
+
+
 class Tape:
     """Device memory of one checkpointed forward (chem_tape)."""
 
@@ -380,6 +390,14 @@ def chem_integrate_fn():
         @staticmethod
         def backward(ctx, gT, gY):
             (P,) = ctx.saved_tensors
+            bad = int((ctx.status != STATUS_OK).sum().item())
+            if bad:
+                # a cell that stopped early (attempt limit, step underflow, full tape, bad input)
+                # did not integrate to dt: its gradient would belong to a different map
+                codes = sorted(set(ctx.status[ctx.status != STATUS_OK].tolist()))
+                raise ChemError("backward through chem_integrate_ckpt: %d cell(s) did not reach "
+                                "dt (status codes %s); enlarge the tape capacity or max_steps"
+                                % (bad, codes))
             T_like = P
             gT = torch.zeros_like(T_like) if gT is None else gT.contiguous()
             gY = (torch.zeros((ctx.mech.ns, P.shape[0]), dtype=torch.float64, device=P.device)

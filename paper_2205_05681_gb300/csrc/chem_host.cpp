@@ -19,6 +19,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <unordered_map>
 #include <vector>
@@ -548,6 +549,7 @@ std::string emit_mechanism(const MechData& m0, int team, int tpb, bool adjoint, 
   emit_array(o, "int", "mk_spseg_beg", "[" + std::to_string(ns + 1) + "]", ns + 1, [&](int i) { return std::to_string(spseg[i]); });
   o << kDeviceSource;
   o << "\nextern \"C\" __device__ const int chem_slots = SLOTS;\n";
+  o << "extern \"C\" __device__ const int chem_tstride = TSTRIDE;\n";
   return o.str();
 }
 
@@ -695,6 +697,14 @@ int slots_for(const MechData& m, int tableau, int team) {
   return ns * ns + (8 + c.s + (needs_f0(c) ? 1 : 0)) * ns + packed * (team == 1 ? 2 : 1) + 24;
 }
 
+// distance in doubles between consecutive teams' slots (TSTRIDE of ros4_device.cuh): sub-warp
+// teams pad to TEAM (mod 16) so that the teams of a half-warp hit disjoint banks
+int tstride_for(const MechData& m, int tableau, int team) {
+  const int sl = slots_for(m, tableau, team);
+  if (team > 1 && team < 32) return sl + ((team - sl % 16 + 16) % 16);
+  return sl;
+}
+
 // default kernel configuration by mechanism size (the autotuner's usual pick on GB300):
 // two warps per cell up to 64 species, eight warps per cell above
 void default_config(int ns, int* team, int* tpb) {
@@ -704,17 +714,19 @@ void default_config(int ns, int* team, int* tpb) {
 
 int check_config(int team, int tpb) {
   if (team == 1 && (tpb == 32 || tpb == 64 || tpb == 128)) return 0;
+  if ((team == 4 || team == 8 || team == 16) && (tpb == 32 || tpb == 64 || tpb == 128)) return 0;
   if (team == 32 && tpb % 32 == 0 && tpb >= 32 && tpb <= 256) return 0;
   if ((team == 64 || team == 128 || team == 256) && tpb == team) return 0;
   return fail(CHEM_EARG, "unsupported kernel config team=%d block=%d", team, tpb);
 }
 
 int smem_bytes(const MechData& m, int team, int tpb, int tableau) {
-  const int teams = team == 1 ? tpb : (team == 32 ? tpb / 32 : 1);
-  return slots_for(m, tableau, team) * 8 * teams;
+  const int teams = team <= 32 ? tpb / team : 1;
+  return tstride_for(m, tableau, team) * 8 * teams;
 }
 
-int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = false, int tableau = 0) {
+int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = false, int tableau = 0,
+               const std::string* prebuilt = nullptr) {
   std::lock_guard<std::mutex> lk(m->mu);
   if (tableau < 0 || tableau > 4) return fail(CHEM_EARG, "unknown integration method %d", tableau);
   auto key = std::make_tuple(team, tpb, tableau);
@@ -730,7 +742,8 @@ int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = fal
   if (smem > max_optin)
     return fail(CHEM_EARG, "config team=%d block=%d needs %d B shared memory (max %d)", team, tpb, smem, max_optin);
   std::string cubin, log;
-  if (int rc = build_cubin(m->data, team, tpb, adjoint, tableau, m->cache_dir.c_str(), m->verbose, &cubin, &log))
+  if (prebuilt && !prebuilt->empty()) cubin = *prebuilt;
+  else if (int rc = build_cubin(m->data, team, tpb, adjoint, tableau, m->cache_dir.c_str(), m->verbose, &cubin, &log))
     return rc;
   auto mod = std::make_unique<Module>();
   mod->team = team;
@@ -751,19 +764,23 @@ int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = fal
   if (dev_slots != slots_for(m->data, tableau, team))
     return fail(CHEM_ECUDA, "shared-memory layout mismatch (%d vs %d)", dev_slots,
                 slots_for(m->data, tableau, team));
+  CU_TRY(drv::cuModuleGetGlobal(&slots_ptr, &slots_sz, mod->mod, "chem_tstride"));
+  CU_TRY(drv::cuMemcpyDtoH(&dev_slots, slots_ptr, sizeof(int)));
+  if (dev_slots != tstride_for(m->data, tableau, team))
+    return fail(CHEM_ECUDA, "team stride mismatch (%d vs %d)", dev_slots, tstride_for(m->data, tableau, team));
   for (CUfunction f : {mod->f_source, mod->f_jac, mod->f_int, mod->f_pinit, mod->f_patt}) {
     CU_TRY(drv::cuFuncSetAttribute(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem));
     // all of L1 as shared memory: occupancy is bounded by the cells' shared-memory footprint
     CU_TRY(drv::cuFuncSetAttribute(f, CU_FUNC_ATTRIBUTE_PREFERRED_SHARED_MEMORY_CARVEOUT, 100));
   }
   CU_TRY(drv::cuOccupancyMaxActiveBlocksPerMultiprocessor(&mod->occ, mod->f_int, tpb, smem));
-  if (adjoint && team > 1) {
+  if (adjoint && team >= 32) {
     CUdeviceptr ap;
     size_t asz;
     CU_TRY(drv::cuModuleGetGlobal(&ap, &asz, mod->mod, "chem_aslots"));
     int aslots = 0;
     CU_TRY(drv::cuMemcpyDtoH(&aslots, ap, sizeof(int)));
-    const int asmem = aslots * 8 * (team == 32 ? tpb / 32 : 1);
+    const int asmem = aslots * 8 * (team <= 32 ? tpb / team : 1);
     if (asmem <= max_optin) {
       CU_TRY(drv::cuModuleGetFunction(&mod->f_adj, mod->mod, "chem_adjoint_k"));
       CU_TRY(drv::cuModuleGetFunction(&mod->f_adjred, mod->mod, "chem_adjoint_reduce_k"));
@@ -786,7 +803,7 @@ int resolve(chem_mech* m, const chem_int_opts* o, Module** mod) {
   int team = m->default_team, tpb = m->default_tpb;
   if (o && o->team > 0) {
     team = o->team;
-    tpb = o->block > 0 ? o->block : (team == 1 ? 64 : (team == 32 ? 64 : team));
+    tpb = o->block > 0 ? o->block : (team <= 32 ? 64 : team);
   }
   return get_module(m, team, tpb, mod, false, o ? o->tableau : 0);
 }
@@ -796,7 +813,7 @@ int make_current(chem_mech* m) {
   return 0;
 }
 
-int teams_per_block(const Module* mod) { return mod->team == 1 ? mod->tpb : (mod->team == 32 ? mod->tpb / 32 : 1); }
+int teams_per_block(const Module* mod) { return mod->team <= 32 ? mod->tpb / mod->team : 1; }
 
 unsigned grid_for(const chem_mech* m, const Module* mod, int64_t n_cells) {
   const int64_t tpb = teams_per_block(mod);
@@ -854,7 +871,7 @@ int chem_mech_compile_only(const char* spec_path, const chem_build_opts* opts, c
   if (int rc = check_config(team, tpb)) return rc;
   std::string cubin, lg;
   const bool adj = opts && opts->adjoint;
-  if (adj && team == 1) return fail(CHEM_EARG, "the adjoint needs a multi-lane configuration (team >= 32)");
+  if (adj && team < 32) return fail(CHEM_EARG, "the adjoint needs a multi-lane configuration (team >= 32)");
   const int tab = opts ? opts->tableau : 0;
   if (tab < 0 || tab > 4) return fail(CHEM_EARG, "unknown integration method %d", tab);
   if (adj && tab != 0) return fail(CHEM_EARG, "the adjoint is implemented for ROS4 (tableau 0)");
@@ -1155,7 +1172,7 @@ static int adjoint_module(chem_mech_t m, const chem_int_opts* o, Module** mod) {
   Module* fwd;
   if (o && o->tableau != 0) return fail(CHEM_EARG, "the adjoint is implemented for ROS4 (tableau 0)");
   if (int rc = resolve(m, o, &fwd)) return rc;
-  if (fwd->team == 1) return fail(CHEM_EARG, "the adjoint needs a multi-lane configuration (team >= 32)");
+  if (fwd->team < 32) return fail(CHEM_EARG, "the adjoint needs a multi-lane configuration (team >= 32)");
   if (int rc = get_module(m, fwd->team, fwd->tpb, mod, true)) return rc;
   if (!(*mod)->f_adj)
     return fail(CHEM_EARG, "the adjoint needs a multi-lane configuration (team >= 32) that fits shared memory");
@@ -1304,6 +1321,112 @@ int chem_eval_vjp(chem_mech_t m, int64_t n_cells, const double* T, const double*
   return 0;
 }
 
+// Throughput probe of the FP64 pipe: independent FMA chains (8 per thread), and chains of exp and
+// log (4 per thread), over a grid of 4 blocks x 256 threads per SM.  Costs are reported per call
+// in units of one FMA's pipe time.
+static const char* const kFp64ProbeSource = R"PROBE(
+extern "C" __global__ void __launch_bounds__(256) probe_fma(double* out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = 1e-3 * threadIdx.x + k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+extern "C" __global__ void __launch_bounds__(256) probe_exp(double* out, int iters) {
+  double x[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) x[k] = 1e-4 * threadIdx.x + 0.1 * k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = exp(-x[k]);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x[0] + x[1] + x[2] + x[3];
+}
+extern "C" __global__ void __launch_bounds__(256) probe_log(double* out, int iters) {
+  double x[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) x[k] = 1e-4 * threadIdx.x + 0.1 * k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = log(x[k] + 2.5);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x[0] + x[1] + x[2] + x[3];
+}
+)PROBE";
+
+int chem_fp64_probe(void* stream, double* dfma_tflops, double* exp_cost, double* log_cost) {
+  if (!drv::load()) return fail(CHEM_ECUDA, "%s", drv::load_error.c_str());
+  CU_TRY(drv::cuInit(0));
+  CUcontext ctx = nullptr;
+  CU_TRY(drv::cuCtxGetCurrent(&ctx));
+  if (!ctx) {
+    CUdevice dev;
+    CU_TRY(drv::cuDeviceGet(&dev, 0));
+    CU_TRY(drv::cuDevicePrimaryCtxRetain(&ctx, dev));
+    CU_TRY(drv::cuCtxSetCurrent(ctx));
+  }
+  CUdevice dev;
+  CU_TRY(drv::cuCtxGetDevice(&dev));
+  int n_sm = 0;
+  CU_TRY(drv::cuDeviceGetAttribute(&n_sm, CU_DEVICE_ATTRIBUTE_MULTIPROCESSOR_COUNT, dev));
+  std::string cubin, log;
+  if (int rc = nvrtc_compile(kFp64ProbeSource, "chem_fp64_probe.cu", &cubin, &log)) return rc;
+  CUmodule mod;
+  CU_TRY(drv::cuModuleLoadData(&mod, cubin.data()));
+  struct Unload { CUmodule m; ~Unload() { drv::cuModuleUnload(m); } } unload{mod};
+  CUfunction f_fma, f_exp, f_log;
+  CU_TRY(drv::cuModuleGetFunction(&f_fma, mod, "probe_fma"));
+  CU_TRY(drv::cuModuleGetFunction(&f_exp, mod, "probe_exp"));
+  CU_TRY(drv::cuModuleGetFunction(&f_log, mod, "probe_log"));
+  const unsigned grid = (unsigned)n_sm * 4, tpb = 256;
+  CUdeviceptr out = 0;
+  CU_TRY(drv::cuMemAlloc(&out, sizeof(double) * grid * tpb));
+  struct Free { CUdeviceptr p; ~Free() { if (p) drv::cuMemFree(p); } } guard{out};
+  CUstream s = (CUstream)stream;
+  CUevent e0, e1;
+  CU_TRY(drv::cuEventCreate(&e0, 0));
+  CU_TRY(drv::cuEventCreate(&e1, 0));
+  // best of 3 timed launches after one warm-up, seconds
+  auto timed = [&](CUfunction f, void** args, double* sec) -> int {
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      CU_TRY(drv::cuEventRecord(e0, s));
+      CU_TRY(drv::cuLaunchKernel(f, grid, 1, 1, tpb, 1, 1, 0, s, args, nullptr));
+      CU_TRY(drv::cuEventRecord(e1, s));
+      CU_TRY(drv::cuEventSynchronize(e1));
+      float ms = 0;
+      CU_TRY(drv::cuEventElapsedTime(&ms, e0, e1));
+      if (rep > 0 && ms < best) best = ms;
+    }
+    *sec = best * 1e-3;
+    return 0;
+  };
+  int it_fma = 8192, it_tr = 1024;
+  double a = 0.999999, b = 1e-6;
+  double t_fma = 0, t_exp = 0, t_log = 0;
+  void* af[] = {&out, &it_fma, &a, &b};
+  void* ae[] = {&out, &it_tr};
+  int rc = timed(f_fma, af, &t_fma);
+  if (!rc) rc = timed(f_exp, ae, &t_exp);
+  if (!rc) rc = timed(f_log, ae, &t_log);
+  drv::cuEventDestroy(e0);
+  drv::cuEventDestroy(e1);
+  if (rc) return rc;
+  const double threads = (double)grid * tpb;
+  const double n_fma = threads * 8.0 * it_fma, n_tr = threads * 4.0 * it_tr;
+  const double per_fma = t_fma / n_fma;
+  if (dfma_tflops) *dfma_tflops = 2.0 * n_fma / t_fma * 1e-12;
+  if (exp_cost) *exp_cost = (t_exp / n_tr) / per_fma;
+  if (log_cost) *log_cost = (t_log / n_tr) / per_fma;  // includes the argument's add (one FP64 op)
+  return 0;
+}
+
 int chem_autotune(chem_mech_t m, int64_t n_cells, const double* T, const double* P, const double* Y, int64_t ld,
                   double dt, double rtol, double atol, void* stream, int32_t* team_out, int32_t* block_out,
                   float* ms_out) {
@@ -1325,15 +1448,46 @@ int chem_autotune(chem_mech_t m, int64_t n_cells, const double* T, const double*
   for (int k = 0; k < ns; ++k)
     CU_TRY(drv::cuMemcpyDtoDAsync(buf + oY0 + 8 * n * k, (CUdeviceptr)(Y + (size_t)k * ld), 8 * n, s));
   std::vector<std::pair<int, int>> cand = {{32, 32}, {32, 64}, {64, 64}, {128, 128}, {256, 256}};
+  // several cells per warp for small mechanisms
+  if (ns <= 32) cand.insert(cand.begin(), {{4, 64}, {8, 64}, {8, 128}, {16, 128}});
+  if (ns <= 64) cand.insert(cand.begin(), {16, 64});
   if (ns <= 16) cand.insert(cand.begin(), {1, 32});
+  // compile the candidates not loaded yet in parallel host threads (NVRTC is thread-safe); the
+  // modules are then loaded one by one
+  std::vector<std::string> cubins(cand.size());
+  {
+    int max_optin = 0;
+    CUdevice dev;
+    CU_TRY(drv::cuCtxGetDevice(&dev));
+    CU_TRY(drv::cuDeviceGetAttribute(&max_optin, CU_DEVICE_ATTRIBUTE_MAX_SHARED_MEMORY_PER_BLOCK_OPTIN, dev));
+    std::vector<int> todo;
+    {
+      std::lock_guard<std::mutex> lk(m->mu);
+      for (size_t i = 0; i < cand.size(); ++i)
+        if (!m->modules.count(std::make_tuple(cand[i].first, cand[i].second, 0)) &&
+            check_config(cand[i].first, cand[i].second) == 0 &&
+            smem_bytes(m->data, cand[i].first, cand[i].second, 0) <= max_optin)
+          todo.push_back((int)i);
+    }
+    std::vector<std::thread> th;
+    for (int i : todo)
+      th.emplace_back([&, i] {
+        std::string lg;
+        if (build_cubin(m->data, cand[i].first, cand[i].second, false, 0, m->cache_dir.c_str(), false,
+                        &cubins[i], &lg))
+          cubins[i].clear();
+      });
+    for (auto& t : th) t.join();
+  }
   CUevent e0, e1;
   CU_TRY(drv::cuEventCreate(&e0, 0));
   CU_TRY(drv::cuEventCreate(&e1, 0));
   float best = 1e30f;
   int bt = m->default_team, bb = m->default_tpb;
-  for (auto& c : cand) {
+  for (size_t ci = 0; ci < cand.size(); ++ci) {
+    const auto& c = cand[ci];
     Module* mod = nullptr;
-    if (get_module(m, c.first, c.second, &mod) != 0) continue;  // does not fit: skip
+    if (get_module(m, c.first, c.second, &mod, false, 0, &cubins[ci]) != 0) continue;  // does not fit: skip
     chem_int_opts o{};
     o.team = c.first;
     o.block = c.second;

@@ -25,8 +25,10 @@
 // Work decomposition.  A "team" of TEAM threads owns one cell at a time; all of the cell's
 // working set (the N x N matrix, stage vectors, thermo and rate scratch) sits in shared memory.
 // TEAM == 1: one thread per cell, arrays interleaved across the block's threads (stride TPB)
-// so that lane-consecutive accesses hit consecutive banks.  TEAM == 32: a warp per cell,
-// contiguous arrays.  TEAM == TPB (64..256): a block per cell.  Reaction loops give each lane a
+// so that lane-consecutive accesses hit consecutive banks.  TEAM == 4, 8, 16: several cells per
+// warp (sub-warp teams, for small mechanisms whose loops would leave most lanes of a wider team
+// idle), contiguous arrays per team, team-masked warp synchronisation and shuffles.  TEAM == 32:
+// a warp per cell.  TEAM == TPB (64..256): a block per cell.  Reaction loops give each lane a
 // subset of reactions and scatter into the shared Jacobian with shared-memory atomics (TEAM>1).
 // Every device loop is bounded; there is no grid-wide wait.
 
@@ -50,19 +52,24 @@
 #define ST_TAPE_FULL 5
 
 #define NEQ NS
-#define NB ((NEQ + 31) / 32)  // 32-row chunks of a state vector held by one warp
+#define NB ((NEQ + WL - 1) / WL)  // WL-row chunks of a state vector held by the first warp
 #define BATH (NS - 1)
 
+#define SUBWARP (TEAM > 1 && TEAM < 32)
 #if TEAM == 1
 #define SS TPB
 #define NTEAM TPB
-#elif TEAM == 32
+#elif TEAM <= 32
 #define SS 1
-#define NTEAM (TPB / 32)
+#define NTEAM (TPB / TEAM)
 #else
 #define SS 1
 #define NTEAM 1
 #endif
+// lanes of the team's first warp (the warp-level parts: pivot scale, stage solves) and the
+// first butterfly offset of a team reduction
+#define WL (TEAM < 32 ? TEAM : 32)
+#define XOR0 (WL / 2)
 
 // per-cell shared-memory slots (units of SS doubles), sized so that eight 53-species cells fit
 // in one SM's shared memory:
@@ -106,12 +113,30 @@
 #endif
 #define OFF_RED (OFF_PERM + PACKED_INTS(NEQ))
 #define SLOTS (OFF_RED + 24)
+// distance between consecutive teams' slots: for sub-warp teams padded to TEAM (mod 16) doubles,
+// so that the teams of a half-warp reading the same offset of their arrays use disjoint banks
+#if SUBWARP
+#define TSTRIDE (SLOTS + ((TEAM - SLOTS % 16 + 16) % 16))
+#else
+#define TSTRIDE SLOTS
+#endif
 #define UOFF(i) ((i) == 0 ? OFF_U1 : OFF_U2 + ((i) - 1) * NEQ)
 
 // ------------------------------------------------------------------------------ team plumbing
 
+// mask of the calling lane's team within its warp (all lanes for TEAM >= 32)
+__device__ __forceinline__ unsigned team_mask() {
+#if SUBWARP
+  return ((1u << TEAM) - 1u) << ((threadIdx.x & 31) & ~(TEAM - 1));
+#else
+  return 0xffffffffu;
+#endif
+}
+
 __device__ __forceinline__ void tsync() {
-#if TEAM == 32
+#if SUBWARP
+  __syncwarp(team_mask());
+#elif TEAM == 32
   __syncwarp();
 #elif TEAM > 32
   __syncthreads();
@@ -140,8 +165,9 @@ __device__ __forceinline__ double team_sum(const Team& tm, double v) {
 #if TEAM == 1
   return v;
 #else
+  const unsigned msk = team_mask();
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = XOR0; o > 0; o >>= 1) v += __shfl_xor_sync(msk, v, o);
 #if TEAM > 32
   double* red = &tm.base[OFF_RED];
   __syncthreads();
@@ -159,8 +185,8 @@ __device__ __forceinline__ double team_sum(const Team& tm, double v) {
 __device__ __forceinline__ bool team_any(const Team& tm, bool f) {
 #if TEAM == 1
   return f;
-#elif TEAM == 32
-  return __any_sync(0xffffffffu, f);
+#elif TEAM <= 32
+  return __any_sync(team_mask(), f);
 #else
   return __syncthreads_or(f) != 0;
 #endif
@@ -614,10 +640,11 @@ __device__ void lu_factor(const Team& tm) {
       const long long v = abs_key(tm.A(i, k));
       if (v > best) { best = v; p = i; }
     }
+    const unsigned msk = team_mask();
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const long long vb = __shfl_xor_sync(0xffffffffu, best, o);
-      const int pb = __shfl_xor_sync(0xffffffffu, p, o);
+    for (int o = XOR0; o > 0; o >>= 1) {
+      const long long vb = __shfl_xor_sync(msk, best, o);
+      const int pb = __shfl_xor_sync(msk, p, o);
       if (vb > best || (vb == best && pb < p)) { best = vb; p = pb; }
     }
 #if TEAM > 32
@@ -640,12 +667,12 @@ __device__ void lu_factor(const Team& tm) {
     // same pipe time whatever its lane count, so the other warps must not repeat the division
     if (tm.tl < 32) {
       const double inv = 1.0 / tm.A(k, k);
-      __syncwarp();  // every lane has read U_kk before lane 0 replaces it by its inverse
+      __syncwarp(msk);  // every lane has read U_kk before lane 0 replaces it by its inverse
       if (tm.tl == 0) {
         tm.invd(k) = inv;
         if (p != k) { const int t = tm.perm(k); tm.perm(k) = tm.perm(p); tm.perm(p) = t; }
       }
-      for (int i = k + 1 + tm.tl; i < NEQ; i += 32) tm.A(i, k) *= inv;
+      for (int i = k + 1 + tm.tl; i < NEQ; i += WL) tm.A(i, k) *= inv;
     }
     tsync();
     const int m = NEQ - k - 1;
@@ -689,24 +716,25 @@ __device__ void lu_solve(const Team& tm, int ob) {
   // and no barrier; the matrix loads do not depend on x and are issued ahead.  The update order
   // per row (k increasing forward, decreasing backward) is that of the column-oriented sweep.
   if (tm.tl < 32) {
-    const int ln = tm.tl & 31;
+    const int ln = tm.tl & (WL - 1);
+    const unsigned msk = team_mask();
     double xr[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
-      const int i = ln + 32 * c;
+      const int i = ln + WL * c;
       xr[c] = i < NEQ ? tm.at(ob, tm.perm(i)) : 0.0;  // P b
     }
     // L (unit lower) forward
 #pragma unroll
     for (int kb = 0; kb < NB; ++kb) {
 #pragma unroll
-      for (int kk = 0; kk < 32; ++kk) {
-        const int k = kb * 32 + kk;
+      for (int kk = 0; kk < WL; ++kk) {
+        const int k = kb * WL + kk;
         if (k < NEQ - 1) {
-          const double xk = __shfl_sync(0xffffffffu, xr[kb], kk);
+          const double xk = __shfl_sync(msk, xr[kb], kk, WL);
 #pragma unroll
           for (int c = kb; c < NB; ++c) {
-            const int i = ln + 32 * c;
+            const int i = ln + WL * c;
             if ((c > kb || ln > kk) && i < NEQ) xr[c] = fma(-tm.A(i, k), xk, xr[c]);
           }
         }
@@ -716,14 +744,14 @@ __device__ void lu_solve(const Team& tm, int ob) {
 #pragma unroll
     for (int kb = NB - 1; kb >= 0; --kb) {
 #pragma unroll
-      for (int kk = 31; kk >= 0; --kk) {
-        const int k = kb * 32 + kk;
+      for (int kk = WL - 1; kk >= 0; --kk) {
+        const int k = kb * WL + kk;
         if (k < NEQ) {
-          const double xk = __shfl_sync(0xffffffffu, xr[kb], kk) * tm.invd(k);
+          const double xk = __shfl_sync(msk, xr[kb], kk, WL) * tm.invd(k);
           if (ln == kk) xr[kb] = xk;
 #pragma unroll
           for (int c = 0; c <= kb; ++c) {
-            const int i = ln + 32 * c;
+            const int i = ln + WL * c;
             if (c < kb || ln < kk) xr[c] = fma(-tm.A(i, k), xk, xr[c]);
           }
         }
@@ -731,7 +759,7 @@ __device__ void lu_solve(const Team& tm, int ob) {
     }
 #pragma unroll
     for (int c = 0; c < NB; ++c) {
-      const int i = ln + 32 * c;
+      const int i = ln + WL * c;
       if (i < NEQ) tm.at(ob, i) = xr[c];
     }
   }
@@ -740,37 +768,38 @@ __device__ void lu_solve(const Team& tm, int ob) {
 }
 
 #if TEAM > 1
-// Column-oriented solve by one warp through shared memory (the adjoint kernels use it: it needs
+// Column-oriented solve by the team's first warp through shared memory (the adjoint kernels use it: it needs
 // no registers for the vector, and the adjoint kernels run at their register cap).
 __device__ void lu_solve_col(const Team& tm, int ob) {
   if (tm.tl < 32) {
-    const int ln = tm.tl & 31;
+    const int ln = tm.tl & (WL - 1);
+    const unsigned msk = team_mask();
     {  // P b through the composed permutation
       double g[NB];
 #pragma unroll
       for (int c = 0; c < NB; ++c) {
-        const int i = ln + 32 * c;
+        const int i = ln + WL * c;
         g[c] = i < NEQ ? tm.at(ob, tm.perm(i)) : 0.0;
       }
-      __syncwarp();
+      __syncwarp(msk);
 #pragma unroll
       for (int c = 0; c < NB; ++c) {
-        const int i = ln + 32 * c;
+        const int i = ln + WL * c;
         if (i < NEQ) tm.at(ob, i) = g[c];
       }
     }
-    __syncwarp();
+    __syncwarp(msk);
     for (int k = 0; k < NEQ - 1; ++k) {
       const double xk = tm.at(ob, k);
-      for (int i = k + 1 + ln; i < NEQ; i += 32) tm.at(ob, i) -= tm.A(i, k) * xk;
-      __syncwarp();
+      for (int i = k + 1 + ln; i < NEQ; i += WL) tm.at(ob, i) -= tm.A(i, k) * xk;
+      __syncwarp(msk);
     }
     for (int k = NEQ - 1; k >= 0; --k) {
       const double xk = tm.at(ob, k) * tm.invd(k);
-      __syncwarp();
-      if (ln == (k & 31)) tm.at(ob, k) = xk;
-      for (int i = ln; i < k; i += 32) tm.at(ob, i) -= tm.A(i, k) * xk;
-      __syncwarp();
+      __syncwarp(msk);
+      if (ln == (k & (WL - 1))) tm.at(ob, k) = xk;
+      for (int i = ln; i < k; i += WL) tm.at(ob, i) -= tm.A(i, k) * xk;
+      __syncwarp(msk);
     }
   }
   tsync();
@@ -952,9 +981,9 @@ __device__ __forceinline__ Team make_team(double* smem) {
 #if TEAM == 1
   tm.base = smem + threadIdx.x;
   tm.tl = 0;
-#elif TEAM == 32
-  tm.base = smem + (threadIdx.x >> 5) * SLOTS;
-  tm.tl = threadIdx.x & 31;
+#elif TEAM <= 32
+  tm.base = smem + (threadIdx.x / TEAM) * TSTRIDE;
+  tm.tl = threadIdx.x & (TEAM - 1);
 #else
   tm.base = smem;
   tm.tl = threadIdx.x;
@@ -1000,8 +1029,8 @@ __device__ __forceinline__ void store_cell(const Team& tm, long long c, double* 
 __device__ __forceinline__ long long team_bcast_ll(const Team& tm, long long v) {
 #if TEAM == 1
   return v;
-#elif TEAM == 32
-  return __shfl_sync(0xffffffffu, v, 0);
+#elif TEAM <= 32
+  return __shfl_sync(team_mask(), v, 0, TEAM);
 #else
   long long* r = reinterpret_cast<long long*>(&tm.base[OFF_RED + 12]);
   if (tm.tl == 0) *r = v;
@@ -1020,7 +1049,7 @@ chem_eval_source_k(long long n_cells, const double* __restrict__ T, const double
                    const double* __restrict__ lnA_ext) {
   extern __shared__ double smem[];
   const Team tm = make_team(smem);
-  const long long team_id = (long long)blockIdx.x * NTEAM + (TEAM == 1 ? threadIdx.x : (TEAM == 32 ? threadIdx.x >> 5 : 0));
+  const long long team_id = (long long)blockIdx.x * NTEAM + (TEAM <= 32 ? threadIdx.x / TEAM : 0);
   const long long stride = (long long)gridDim.x * NTEAM;
   for (long long c = team_id; c < n_cells; c += stride) {
     if (tm.tl == 0) tm.at(OFF_Y, 0) = T[c];
@@ -1038,7 +1067,7 @@ chem_eval_jacobian_k(long long n_cells, const double* __restrict__ T, const doub
                      const double* __restrict__ lnA_ext) {
   extern __shared__ double smem[];
   const Team tm = make_team(smem);
-  const long long team_id = (long long)blockIdx.x * NTEAM + (TEAM == 1 ? threadIdx.x : (TEAM == 32 ? threadIdx.x >> 5 : 0));
+  const long long team_id = (long long)blockIdx.x * NTEAM + (TEAM <= 32 ? threadIdx.x / TEAM : 0);
   const long long stride = (long long)gridDim.x * NTEAM;
   for (long long c = team_id; c < n_cells; c += stride) {
     if (tm.tl == 0) tm.at(OFF_Y, 0) = T[c];
@@ -1056,7 +1085,8 @@ chem_eval_jacobian_k(long long n_cells, const double* __restrict__ T, const doub
 // Registers capped so that the cells that fit in shared memory can all be resident: eight
 // 64-lane teams (53 species) or two 256-lane teams (111 species) per SM (GB300, 53 species
 // at seven teams: 24.2K vs 22.7K cells/s with the cap)
-#define MIN_BLOCKS (TEAM == 64 ? 8 : (TEAM >= 128 ? 2 : 1))
+// (sub-warp teams: 512 threads per SM, 128 registers a thread)
+#define MIN_BLOCKS (TEAM == 64 ? 8 : (TEAM >= 128 ? 2 : (SUBWARP ? 512 / TPB : 1)))
 extern "C" __global__ void __launch_bounds__(TPB, MIN_BLOCKS)
 chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __restrict__ P,
                  double* __restrict__ Y, long long ld, double dt, double rtol, double atol,
@@ -1071,6 +1101,7 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
   double Pc = 0.0;
   Ctl c;
   c.done = true;
+  c.acc = false;
   int nacc = 0;
   // bounded: every iteration either retires a cell or makes an attempt (<= max_steps per cell)
   for (;;) {
@@ -1102,19 +1133,21 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
       if (tape_ck)  // checkpoint 0: the initial state
         for (int i = tm.tl; i < NEQ; i += TEAM) tape_ck[(long long)i * n_cells + cell] = tm.at(OFF_Y, i);
     }
-    ros4_advance(tm, c, Pc, dt, rtol, atol, max_steps, h_min, lnA_ext);
-    if (tape_h && c.acc) {
+    if (tape_h && nacc >= tape_cap) {
+      // the tape holds no further step: stop before attempting one, so that the stored state is
+      // exactly the map the tape records (the adjoint then differentiates what was returned)
+      c.status = ST_TAPE_FULL;
+      c.done = true;
+    } else {
+      ros4_advance(tm, c, Pc, dt, rtol, atol, max_steps, h_min, lnA_ext);
+    }
+    if (tape_h && c.acc && c.status != ST_TAPE_FULL) {
       // record the accepted step; checkpoint the state after every `interval` accepted steps
-      if (nacc < tape_cap) {
-        if (tm.tl == 0) tape_h[(long long)nacc * n_cells + cell] = c.hh;
-        ++nacc;
-        if (nacc % interval == 0 && nacc < tape_cap)
-          for (int i = tm.tl; i < NEQ; i += TEAM)
-            tape_ck[((long long)(nacc / interval) * NEQ + i) * n_cells + cell] = tm.at(OFF_Y, i);
-      } else {
-        c.status = ST_TAPE_FULL;
-        c.done = true;
-      }
+      if (tm.tl == 0) tape_h[(long long)nacc * n_cells + cell] = c.hh;
+      ++nacc;
+      if (nacc % interval == 0 && nacc < tape_cap)
+        for (int i = tm.tl; i < NEQ; i += TEAM)
+          tape_ck[((long long)(nacc / interval) * NEQ + i) * n_cells + cell] = tm.at(OFF_Y, i);
     }
     if (c.done) {
       if (tm.tl == 0 && tape_nacc) tape_nacc[cell] = nacc;
@@ -1147,7 +1180,7 @@ chem_plain_init_k(long long n_cells, const double* __restrict__ T, const double*
                   double* wy, double* wt, double* wh, int* wflags, int* watt, int* wst) {
   extern __shared__ double smem[];
   const Team tm = make_team(smem);
-  const long long team_id = (long long)blockIdx.x * NTEAM + (TEAM == 1 ? threadIdx.x : (TEAM == 32 ? threadIdx.x >> 5 : 0));
+  const long long team_id = (long long)blockIdx.x * NTEAM + (TEAM <= 32 ? threadIdx.x / TEAM : 0);
   const long long stride = (long long)gridDim.x * NTEAM;
   for (long long c = team_id; c < n_cells; c += stride) {
     const bool ok = load_cell(tm, c, T, Y, ld);
@@ -1176,7 +1209,7 @@ chem_plain_attempt_k(long long n_cells, double* __restrict__ T, const double* __
                      int* watt, int* wst, unsigned int* active_count) {
   extern __shared__ double smem[];
   const Team tm = make_team(smem);
-  const long long team_id = (long long)blockIdx.x * NTEAM + (TEAM == 1 ? threadIdx.x : (TEAM == 32 ? threadIdx.x >> 5 : 0));
+  const long long team_id = (long long)blockIdx.x * NTEAM + (TEAM <= 32 ? threadIdx.x / TEAM : 0);
   const long long stride = (long long)gridDim.x * NTEAM;
   for (long long cell = team_id; cell < n_cells; cell += stride) {
     const int fl = wflags[cell];
@@ -1232,7 +1265,7 @@ extern "C" __global__ void chem_plain_finish_k(long long n_cells, int* __restric
 // initial state, through the ROS4 steps with the accepted step sizes frozen (Sec. 2.3 algebra,
 // differentiated).  Only built for multi-lane teams (contiguous shared-memory layout), and only
 // into the separately compiled adjoint module (CHEM_ADJOINT) so that forward modules compile fast.
-#if TEAM > 1 && defined(CHEM_ADJOINT) && TABLEAU_ID == 0
+#if TEAM >= 32 && defined(CHEM_ADJOINT) && TABLEAU_ID == 0
 
 // forward-mode dual number: value and one directional derivative
 struct DD {
@@ -1798,10 +1831,10 @@ chem_eval_vjp_k(long long n_cells, const double* __restrict__ T, const double* _
   }
 }
 
-#endif  // TEAM > 1 && CHEM_ADJOINT
+#endif  // TEAM >= 32 && CHEM_ADJOINT
 
 extern "C" __device__ const int chem_aslots =
-#if TEAM > 1 && defined(CHEM_ADJOINT) && TABLEAU_ID == 0
+#if TEAM >= 32 && defined(CHEM_ADJOINT) && TABLEAU_ID == 0
     ASLOTS;
 #else
     0;

@@ -524,10 +524,14 @@ def make_states(mech: Mechanism, n_cells: int, recipe: str, seed: int) -> States
       ``ch4_partial``  T~U(800,2200), P~U(1,50) atm, phi~U(0.5,2), Y = (1-xi)*unburnt + xi*products,
                        xi~U(0,1), plus a log-uniform 1e-8..1e-3 radical pool, renormalised
       ``ch4_front``    90% near-equilibrium products at U(1800,2400) K with a 1e-6..1e-4 radical pool,
-                       10% ignition-front fresh mixture at U(1000,1300) K with a 1e-8..1e-5 pool,
-                       randomly interleaved; P~U(1,50) atm
-      ``ch4_ign``      fresh mixture, phi~U(0.5,2), T~U(900,1400), P~U(1,40) atm, pool 1e-8..1e-6
-      ``ch4_ign_wide`` as ``ch4_ign`` with T~U(900,1500), P~U(1,50) atm
+                       10% ignition-front cells at U(1000,1300) K: (1-xi)*unburnt + xi*products,
+                       xi~U(0,0.5), phi~U(0.5,1.5), with a 1e-6..1e-2 radical pool (the radical-rich
+                       reaction zone; over 20 split steps of 1 us these need 10-20x the step
+                       attempts of the relaxed product cells), randomly interleaved; P~U(1,50) atm
+      ``ch4_ign``      fresh mixture, phi~U(0.5,2), T~U(900,1400), P~U(1,40) atm, seeded with a
+                       1e-4..3e-2 radical pool (by mass, renormalised) so that the cells ignite
+                       within 1e-4 s (median temperature rise ~540 K, a tenth above 1000 K)
+      ``ch4_ign_wide`` fresh mixture, phi~U(0.5,2), T~U(900,1500), P~U(1,50) atm, pool 1e-8..1e-6
     """
     rng = np.random.default_rng(seed)
     C = n_cells
@@ -556,7 +560,9 @@ def make_states(mech: Mechanism, n_cells: int, recipe: str, seed: int) -> States
             T = rng.uniform(900.0, Tmax, C)
             P = rng.uniform(1.0, Pmax, C) * ATM
             xi = np.zeros(C)
-            lo, hi = 1e-8, 1e-6
+            # ch4_ign: radical-seeded cells that ignite within 1e-4 s (a trace pool leaves these
+            # mixtures in their induction period over that interval)
+            lo, hi = (1e-4, 3e-2) if recipe == "ch4_ign" else (1e-8, 1e-6)
         phi = rng.uniform(0.5, 2.0, C)
         Y = np.zeros((C, ns))
         for i in range(C):
@@ -569,12 +575,15 @@ def make_states(mech: Mechanism, n_cells: int, recipe: str, seed: int) -> States
         T = np.where(front, rng.uniform(1000.0, 1300.0, C), rng.uniform(1800.0, 2400.0, C))
         P = rng.uniform(1.0, 50.0, C) * ATM
         phi = np.where(front, rng.uniform(0.5, 1.5, C), rng.uniform(0.7, 1.3, C))
+        xi = rng.uniform(0.0, 0.5, C)  # progress of a front cell between unburnt and burnt
         pool_b = _radical_pool(mech, rng, C, 1e-6, 1e-4, main)
-        pool_f = _radical_pool(mech, rng, C, 1e-8, 1e-5, main)
+        pool_f = _radical_pool(mech, rng, C, 1e-6, 1e-2, main)
         Y = np.zeros((C, ns))
         for i in range(C):
             if front[i]:
-                Y[i] = _mole_to_mass(mech, _fuel_air(mech, fuel, phi[i])) + pool_f[i]
+                Yu = _mole_to_mass(mech, _fuel_air(mech, fuel, phi[i]))
+                Yb = _mole_to_mass(mech, _products(mech, fuel, phi[i]))
+                Y[i] = (1 - xi[i]) * Yu + xi[i] * Yb + pool_f[i]
             else:
                 Y[i] = _mole_to_mass(mech, _products(mech, fuel, phi[i])) + pool_b[i]
     else:

@@ -62,3 +62,15 @@ def test_adjoint_module_compiles_and_refuses_other_methods(tmp_path):
         chem.compile_only(mech, team=64, block=64, cache_dir=str(tmp_path), adjoint=True, tableau=1)
     with pytest.raises(chem.ChemError, match="unknown integration method"):
         chem.compile_only(mech, team=64, block=64, cache_dir=str(tmp_path), tableau=7)
+
+
+@pytest.mark.parametrize("team,block", [(4, 64), (8, 128), (16, 64)])
+def test_subwarp_teams_compile(tmp_path, team, block):
+    """Several cells per warp (4-, 8- and 16-lane teams) generate and compile for sm_103a."""
+    from paper_2205_05681_gb300 import chem
+    log = chem.compile_only(os.path.join(ROOT, "tests", "golden", "tiny_hon7.mech"), team=team,
+                            block=block, cache_dir=str(tmp_path))
+    assert "sm_103a" in log and "chem_integrate_k" in log
+    with pytest.raises(chem.ChemError, match="adjoint"):
+        chem.compile_only(os.path.join(ROOT, "tests", "golden", "tiny_hon7.mech"), team=team,
+                          block=block, cache_dir=str(tmp_path), adjoint=True)

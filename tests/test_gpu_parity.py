@@ -21,8 +21,8 @@ pytestmark = pytest.mark.gpu
 
 WORK = {"h2_13": "h2_fresh", "ch4_53": "ch4_partial", "ch4_111": "ch4_front"}
 CONFIGS = {
-    "h2_13": [(1, 32), (32, 64), (32, 128), (64, 64), (128, 128)],
-    "ch4_53": [(32, 32), (32, 64), (64, 64), (128, 128), (256, 256)],
+    "h2_13": [(1, 32), (4, 64), (8, 128), (16, 128), (32, 64), (32, 128), (64, 64), (128, 128)],
+    "ch4_53": [(16, 64), (32, 32), (32, 64), (64, 64), (128, 128), (256, 256)],
     "ch4_111": [(32, 32), (128, 128), (256, 256)],
 }
 PARAMS = [(n, t, b) for n in CONFIGS for (t, b) in CONFIGS[n]]
@@ -117,7 +117,7 @@ def test_plain_driver_matches_persistent(omech, gmech, name):
     import torch
     from paper_2205_05681_gb300 import chem
     om = omech(name)
-    team, block = CONFIGS[name][1]
+    team, block = {"h2_13": (8, 128), "ch4_53": (32, 64)}[name]
     g = gmech(name, team, block)
     n = 300
     st, y0 = _inputs(om, name, n, 104)
@@ -139,31 +139,78 @@ def test_plain_driver_matches_persistent(omech, gmech, name):
     assert np.allclose(h1[same], h2[same], rtol=1e-6)
 
 
-def test_full_size_sampled_53(omech, gmech):
-    """65,536 cells of the 53-species workload in the launch configuration the bench times;
-    a sample of cells against the oracle one by one."""
+def _bench_config_mech(mech_path, name):
+    """The mechanism as bench.py loads it: no kernel override, so the launch configuration is the
+    library's default for this mechanism size (chem_kernel_config reports it)."""
+    return gpu_mech(mech_path(name))
+
+
+def _sampled_parity(om, st, g, n, n_sample, seed, label):
+    """Integrate all n cells in one call (default launch configuration) and compare a seeded
+    sample of cells, plus the last cell (ragged tail of the work queue), with the oracle."""
     import torch
-    name = "ch4_53"
-    om = omech(name)
-    team, block = CONFIGS[name][1]
-    g = gmech(name, team, block)
-    n = 65536
-    st = states(name, n, WORK[name], 8)
     T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
     att = torch.zeros(n, dtype=torch.int32, device=T.device)
     status = torch.full((n,), -1, dtype=torch.int32, device=T.device)
     g.integrate(T, P, Y, 1e-6, status=status, opts=g.opts(attempts=att))
     assert (status.cpu().numpy() == 0).all()
-    rng = np.random.default_rng(0)
-    idx = np.sort(rng.choice(n, 48, replace=False))
-    idx[-1] = n - 1  # the ragged tail of the last block
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(n - 1, n_sample - 1, replace=False))
+    idx = np.append(idx, n - 1)
     yg = gpu_state(om, T, Y)[idx]
     y0 = om.state_from_TY(st.T[idx], st.Y[idx])
 
     class Sub:
         P = st.P[idx]
 
-    _check_integration(om, Sub, y0, yg, att.cpu().numpy()[idx], 1e-6, "full53")
+    _check_integration(om, Sub, y0, yg, att.cpu().numpy()[idx], 1e-6, label)
+    return att.cpu().numpy()
+
+
+def _resident_teams(g):
+    """Teams of the persistent launch: SMs x resident blocks x teams per block."""
+    import torch
+    cfg = g.kernel_config()
+    per_block = cfg["block"] if cfg["team"] == 1 else max(1, cfg["block"] // cfg["team"])
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return cfg, sms, per_block
+
+
+def test_full_size_sampled_53(omech, mech_path):
+    """65,536 cells of the 53-species workload in the launch configuration the bench times (the
+    library default, two warps per cell), so every team pulls many cells from the queue; a
+    sample of cells against the oracle one by one."""
+    name = "ch4_53"
+    om = omech(name)
+    g = _bench_config_mech(mech_path, name)
+    cfg = g.kernel_config()
+    assert (cfg["team"], cfg["block"]) == (64, 64)
+    n = 65536
+    st = states(name, n, WORK[name], 8)
+    _sampled_parity(om, st, g, n, 48, 0, "full53")
+
+
+def test_full_size_sampled_111_refill(omech, mech_path):
+    """The 111-species default (256 lanes per cell, register-resident stage solves) on at least
+    three cells per resident team, so that every team refills from the queue at least twice."""
+    name = "ch4_111"
+    om = omech(name)
+    g = _bench_config_mech(mech_path, name)
+    cfg, sms, per_block = _resident_teams(g)
+    assert (cfg["team"], cfg["block"]) == (256, 256)
+    n = 3 * sms * 2 * per_block + 17  # two resident blocks per SM, plus a ragged tail
+    st = states(name, n, "ch4_partial", 21)
+    _sampled_parity(om, st, g, n, 40, 1, "refill111")
+
+
+def test_full_size_sampled_13_wide(omech, mech_path):
+    """The 13-species cells at the 65,536-cell batch (h2_13_wide) in the default configuration."""
+    name = "h2_13"
+    om = omech(name)
+    g = _bench_config_mech(mech_path, name)
+    n = 65536
+    st = states(name, n, "h2_fresh", 12)
+    _sampled_parity(om, st, g, n, 64, 2, "wide13")
 
 
 def test_edge_cases(omech, gmech):
@@ -273,7 +320,8 @@ def test_autotune_picks_a_valid_config(omech, mech_path):
     st, y0 = _inputs(om, name, 512, 110)
     T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
     pick = g.autotune(T, P, Y, 1e-6)
-    assert (pick["team"], pick["block"]) in [(1, 32), (32, 32), (32, 64), (64, 64), (128, 128),
+    assert (pick["team"], pick["block"]) in [(1, 32), (4, 64), (8, 64), (8, 128), (16, 64),
+                                             (16, 128), (32, 32), (32, 64), (64, 64), (128, 128),
                                              (256, 256)]
     assert pick["sample_ms"] > 0
     cfg = g.kernel_config()
@@ -284,46 +332,145 @@ def test_autotune_picks_a_valid_config(omech, mech_path):
     assert weighted_norm(yo, gpu_state(om, T, Y)).max() <= 1e-5
 
 
-def test_cuda_graph_of_split_steps(omech, gmech):
-    """Three consecutive split steps (h carried) captured in one CUDA graph and replayed give the
-    eager result and the oracle's."""
+def _oracle_splits(om, y0, P, dt, nsplit, rtol=1e-6, atol=1e-10):
+    """The oracle over consecutive split steps with h carried: final state and per-split attempts."""
+    y, hh = y0.copy(), np.zeros(len(y0))
+    att = np.zeros((nsplit, len(y0)), dtype=np.int64)
+    for s in range(nsplit):
+        y, info = om.integrate(y, P, dt, rtol=rtol, atol=atol, h=hh, threads=16)
+        assert np.all(info["status"] == 0)
+        att[s] = info["attempts"]
+        hh = info["h"]
+    return y, att
+
+
+def _check_split_sequence(om, P, y0, yg, att_gpu, dt, label):
+    """Multi-split form of the flip rule: cells whose per-split attempt counts all equal the
+    oracle's must be within 1e-5 in the weighted norm; cells where round-off flipped an
+    accept/reject decision in any split step (at most 2% of cells) must lie within 10 tolerance
+    units of the oracle at rtol 1e-10 over the same split steps."""
+    nsplit = att_gpu.shape[0]
+    yo, att_o = _oracle_splits(om, y0, P, dt, nsplit)
+    same = np.all(att_o == att_gpu, axis=0)
+    e = weighted_norm(yo, yg)
+    assert np.all(e[same] <= 1e-5), (label, e[same].max(), np.argmax(np.where(same, e, 0)))
+    flips = np.where(~same)[0]
+    assert len(flips) <= max(1, int(0.02 * len(same))), (label, len(flips))
+    if len(flips):
+        yt, _ = _oracle_splits(om, y0[flips], P[flips], dt, nsplit, rtol=1e-10, atol=1e-14)
+        assert np.all(weighted_norm(yt, yg[flips]) <= 10.0), label
+    return e, att_o
+
+
+def _capture_splits(g, T, P, Y, h, ws, dt, nsplit, att, att_hist):
+    """nsplit consecutive split steps (h carried) captured in one CUDA graph; per-split attempt
+    counts copied into att_hist[s] inside the graph."""
     import torch
-    name = "ch4_53"
-    om = omech(name)
-    g = gmech(name, 64, 64)
-    n = 96
-    st, y0 = _inputs(om, name, n, 111)
-    T0, P, Y0 = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
 
-    def run(T, Y, h, ws):
-        for _ in range(3):
-            g.integrate(T, P, Y, 1e-6, h=h, workspace=ws)
+    def body():
+        for s in range(nsplit):
+            g.integrate(T, P, Y, dt, h=h, opts=g.opts(attempts=att), workspace=ws)
+            att_hist[s].copy_(att)
 
-    T, Y = T0.clone(), Y0.clone()
-    h = torch.zeros(n, dtype=torch.float64, device=T.device)
-    ws = g.workspace(n)
-    run(T, Y, h, ws)
-    eager = [x.cpu().numpy() for x in (T, Y, h)]
-    T.copy_(T0)
-    Y.copy_(Y0)
-    h.zero_()
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=s):
-        run(T, Y, h, ws)
-    T.copy_(T0)
-    Y.copy_(Y0)
-    h.zero_()
+        body()
+    return graph, body
+
+
+def test_cuda_graph_of_split_steps(omech, gmech):
+    """Three consecutive split steps (h carried) captured in one CUDA graph and replayed give the
+    eager result (to rounding) and the oracle's within the parity bound."""
+    import torch
+    name = "ch4_53"
+    om = omech(name)
+    g = gmech(name, 64, 64)
+    n, nsplit = 96, 3
+    st, y0 = _inputs(om, name, n, 111)
+    T0, P, Y0 = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    T, Y = T0.clone(), Y0.clone()
+    h = torch.zeros(n, dtype=torch.float64, device=T.device)
+    att = torch.zeros(n, dtype=torch.int32, device=T.device)
+    hist = torch.zeros((nsplit, n), dtype=torch.int32, device=T.device)
+    ws = g.workspace(n)
+    graph, body = _capture_splits(g, T, P, Y, h, ws, 1e-6, nsplit, att, hist)
+    T.copy_(T0); Y.copy_(Y0); h.zero_(); hist.zero_()
+    body()  # eager
+    torch.cuda.synchronize()
+    eager = [x.cpu().numpy() for x in (T, Y, h, hist)]
+    T.copy_(T0); Y.copy_(Y0); h.zero_(); hist.zero_()
     graph.replay()
     torch.cuda.synchronize()
-    for a, b in zip(eager, (T, Y, h)):
+    # the team's shared-memory atomics sum in a run-dependent order: equal to rounding
+    for a, b in zip(eager[:3], (T, Y, h)):
         assert np.allclose(b.cpu().numpy(), a, rtol=1e-9, atol=1e-18)
-    y, hh = y0.copy(), np.zeros(n)
-    for _ in range(3):
-        y, info = om.integrate(y, st.P, 1e-6, h=hh, threads=16)
-        hh = info["h"]
-    assert weighted_norm(y, gpu_state(om, T, Y)).max() <= 1e-4
+    assert (hist.cpu().numpy() == eager[3]).all(axis=0).mean() >= 0.98
+    _check_split_sequence(om, st.P, y0, gpu_state(om, T, Y), hist.cpu().numpy(), 1e-6, "graph53")
+
+
+def _front_inputs(om, n, seed, n_templates=8, t_relax=1e-3):
+    """Flame-front workload on n cells: ignition-front cells as generated; the near-equilibrium
+    product cells are n_templates product states relaxed by the oracle for t_relax and tiled
+    with a 1e-9 relative perturbation of the mass fractions (the oracle prepares the inputs of
+    both sides)."""
+    st = states("ch4_111", n, "ch4_front", seed)
+    y0 = om.state_from_TY(st.T, st.Y)
+    prod = np.where(st.T >= 1500.0)[0]
+    k = min(n_templates, len(prod))
+    yt, info = om.integrate(y0[prod[:k]], st.P[prod[:k]], t_relax, threads=16)
+    assert np.all(info["status"] == 0)
+    Tt, Yt = om.TY_from_state(yt)
+    rng = np.random.default_rng(seed + 1)
+    src = np.arange(len(prod)) % k
+    T, P, Y = st.T.copy(), st.P.copy(), st.Y.copy()
+    T[prod] = Tt[src]
+    P[prod] = st.P[prod[:k]][src]
+    Yp = Yt[src] * (1.0 + 1e-9 * rng.standard_normal((len(prod), Yt.shape[1])))
+    Y[prod] = Yp / Yp.sum(axis=1, keepdims=True)
+
+    class St:
+        pass
+
+    out = St()
+    out.T, out.P, out.Y = T, P, Y
+    return out, prod
+
+
+def test_config3_graph_20_splits_111(omech, mech_path):
+    """The batched flame-front configuration: 111 species, relaxed product cells interleaved with
+    ignition-front cells, 20 split steps (h carried) replayed from one captured CUDA graph in the
+    default launch configuration, more cells than resident teams; sampled front and product cells
+    against the oracle over the same 20 split steps."""
+    import torch
+    name = "ch4_111"
+    om = omech(name)
+    g = _bench_config_mech(mech_path, name)
+    n, nsplit, dt = 4096, 20, 1e-6
+    st, prod = _front_inputs(om, n, 9)
+    T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    h = torch.zeros(n, dtype=torch.float64, device=T.device)
+    att = torch.zeros(n, dtype=torch.int32, device=T.device)
+    hist = torch.zeros((nsplit, n), dtype=torch.int32, device=T.device)
+    ws = g.workspace(n)
+    T0, Y0 = T.clone(), Y.clone()
+    graph, body = _capture_splits(g, T, P, Y, h, ws, dt, nsplit, att, hist)
+    T.copy_(T0); Y.copy_(Y0); h.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    hist_np = hist.cpu().numpy()
+    tot = hist_np.sum(axis=0)
+    front = np.setdiff1d(np.arange(n), prod)
+    # the stated stiffness contrast: front cells need >= 10x the attempts of the median cell
+    assert tot[front].max() >= 10 * np.median(tot), (tot[front].max(), np.median(tot))
+    rng = np.random.default_rng(5)
+    idx = np.sort(np.concatenate([rng.choice(front, 24, replace=False),
+                                  rng.choice(prod, 24, replace=False)]))
+    yg = gpu_state(om, T, Y)[idx]
+    y0 = om.state_from_TY(st.T[idx], st.Y[idx])
+    _check_split_sequence(om, st.P[idx], y0, yg, hist_np[:, idx], dt, "config3")
+    assert (h.cpu().numpy() > 0).all()
 
 
 @pytest.mark.parametrize("tab", [1, 2, 3])
