@@ -62,8 +62,9 @@ typedef struct chem_mech* chem_mech_t;
 
 /* Options for chem_mech_load (NULL = defaults). */
 typedef struct {
-  int32_t team;        /* lanes per cell for the default kernel config: 1, 32, 64, 128, 256;
-                          0 = chosen from the mechanism size */
+  int32_t team;        /* lanes per cell for the default kernel config: 1 (block 32..128), 4, 8
+                          or 16 (several cells per warp; block 32..128), 32 (block 32..256), 64,
+                          128, 256 (block = team); 0 = chosen from the mechanism size */
   int32_t block;       /* threads per block; 0 = chosen with team */
   int32_t verbose;     /* print compile logs (register use) to stderr */
   const char* cache_dir; /* directory for compiled cubins; NULL = no disk cache */
@@ -240,13 +241,16 @@ int chem_eval_vjp(chem_mech_t mech, int64_t n_cells, const double* T, const doub
                   const double* n, const double* v, double* gy, double* gp, int64_t ld,
                   const double* lnA, void* stream);
 
-/* Autotuner: picks the fastest kernel configuration (lanes per cell "team" and threads per
- * block) for this mechanism by integrating a sample of the caller's cells (the first
- * min(n_cells, 4096) of T, P, Y [Ns x ld]) once per candidate configuration that fits in shared
- * memory, and makes it the mechanism's default.  The caller's arrays are not modified (the sample
- * is copied).  Candidate modules are compiled on first use (NVRTC; cached in cache_dir).
- * Set-up time only: allocates temporary device memory and synchronises `stream`.  Outputs
- * (nullable): the chosen team and block and the sample's integration time in ms.
+/* Autotuner: picks the fastest kernel configuration (lanes per cell "team" -- from several
+ * cells per warp (4, 8, 16 lanes) for small mechanisms up to a block of 256 lanes per cell -- and
+ * threads per block) for this mechanism by integrating a sample of the caller's cells once per
+ * candidate configuration that fits in shared memory, and makes it the mechanism's default.  The
+ * sample is the first min(n_cells, max(4096, 4 x the most resident cells of any candidate)) cells
+ * of T, P, Y [Ns x ld], so that every candidate runs at full occupancy.  The caller's arrays are
+ * not modified (the sample is copied).  Candidate modules are compiled on first use, in parallel
+ * host threads (NVRTC; cached in cache_dir).  Set-up time only: allocates temporary device memory
+ * and synchronises `stream`.  Outputs (nullable): the chosen team and block and the sample's
+ * integration time in ms.
  * (Not from the paper, which tunes nothing at run time: its vector width is fixed at 8.) */
 int chem_autotune(chem_mech_t mech, int64_t n_cells, const double* T, const double* P,
                   const double* Y, int64_t ld, double dt, double rtol, double atol, void* stream,

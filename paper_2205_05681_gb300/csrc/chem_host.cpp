@@ -1435,18 +1435,7 @@ int chem_autotune(chem_mech_t m, int64_t n_cells, const double* T, const double*
   if (n_cells == 0 || !T || !P || !Y) return fail(CHEM_EARG, "autotune needs a non-empty sample");
   if (int rc = make_current(m)) return rc;
   const int ns = (int)m->data.sp.size();
-  const int64_t n = std::min<int64_t>(n_cells, 4096);
   CUstream s = (CUstream)stream;
-  // private copy of the sample: T, P, Y [ns][n], h, workspace
-  const size_t oT = 0, oP = align256(8 * n), oY = align256(oP + 8 * n), oY0 = align256(oY + 8 * n * ns),
-               oT0 = align256(oY0 + 8 * n * ns), oW = align256(oT0 + 8 * n), total = oW + 256;
-  CUdeviceptr buf = 0;
-  CU_TRY(drv::cuMemAlloc(&buf, total));
-  struct Free { CUdeviceptr p; ~Free() { if (p) drv::cuMemFree(p); } } guard{buf};
-  CU_TRY(drv::cuMemcpyDtoDAsync(buf + oT0, (CUdeviceptr)T, 8 * n, s));
-  CU_TRY(drv::cuMemcpyDtoDAsync(buf + oP, (CUdeviceptr)P, 8 * n, s));
-  for (int k = 0; k < ns; ++k)
-    CU_TRY(drv::cuMemcpyDtoDAsync(buf + oY0 + 8 * n * k, (CUdeviceptr)(Y + (size_t)k * ld), 8 * n, s));
   std::vector<std::pair<int, int>> cand = {{32, 32}, {32, 64}, {64, 64}, {128, 128}, {256, 256}};
   // several cells per warp for small mechanisms
   if (ns <= 32) cand.insert(cand.begin(), {{4, 64}, {8, 64}, {8, 128}, {16, 128}});
@@ -1479,6 +1468,28 @@ int chem_autotune(chem_mech_t m, int64_t n_cells, const double* T, const double*
       });
     for (auto& t : th) t.join();
   }
+  // the sample: enough cells for four waves of the widest candidate's resident teams (at least
+  // 4096), so that every candidate is timed at full occupancy
+  std::vector<Module*> mods(cand.size(), nullptr);
+  int64_t resident = 0;
+  for (size_t ci = 0; ci < cand.size(); ++ci) {
+    if (get_module(m, cand[ci].first, cand[ci].second, &mods[ci], false, 0, &cubins[ci]) != 0) {
+      mods[ci] = nullptr;  // does not fit: skip
+      continue;
+    }
+    resident = std::max<int64_t>(resident, (int64_t)m->n_sm * mods[ci]->occ * teams_per_block(mods[ci]));
+  }
+  const int64_t n = std::min<int64_t>(n_cells, std::max<int64_t>(4096, 4 * resident));
+  // private copy of the sample: T, P, Y [ns][n], h, workspace
+  const size_t oT = 0, oP = align256(8 * n), oY = align256(oP + 8 * n), oY0 = align256(oY + 8 * n * ns),
+               oT0 = align256(oY0 + 8 * n * ns), oW = align256(oT0 + 8 * n), total = oW + 256;
+  CUdeviceptr buf = 0;
+  CU_TRY(drv::cuMemAlloc(&buf, total));
+  struct Free { CUdeviceptr p; ~Free() { if (p) drv::cuMemFree(p); } } guard{buf};
+  CU_TRY(drv::cuMemcpyDtoDAsync(buf + oT0, (CUdeviceptr)T, 8 * n, s));
+  CU_TRY(drv::cuMemcpyDtoDAsync(buf + oP, (CUdeviceptr)P, 8 * n, s));
+  for (int k = 0; k < ns; ++k)
+    CU_TRY(drv::cuMemcpyDtoDAsync(buf + oY0 + 8 * n * k, (CUdeviceptr)(Y + (size_t)k * ld), 8 * n, s));
   CUevent e0, e1;
   CU_TRY(drv::cuEventCreate(&e0, 0));
   CU_TRY(drv::cuEventCreate(&e1, 0));
@@ -1486,8 +1497,7 @@ int chem_autotune(chem_mech_t m, int64_t n_cells, const double* T, const double*
   int bt = m->default_team, bb = m->default_tpb;
   for (size_t ci = 0; ci < cand.size(); ++ci) {
     const auto& c = cand[ci];
-    Module* mod = nullptr;
-    if (get_module(m, c.first, c.second, &mod, false, 0, &cubins[ci]) != 0) continue;  // does not fit: skip
+    if (!mods[ci]) continue;
     chem_int_opts o{};
     o.team = c.first;
     o.block = c.second;

@@ -603,6 +603,8 @@ __device__ void eval_f_jac(const Team& tm, int oy, int of, double P, const doubl
 
 // ------------------------------------------------------------------------------ LU + solves
 
+#define LU_W 8  // panel width of the blocked LU of block-per-cell teams
+
 // In-place LU with partial pivoting of A (N x N): largest |a| in the column, lowest row on
 // ties.  1/U_kk replaces U_kk on the diagonal, the composed row permutation (row i of P A is row
 // perm[i] of A) goes to OFF_PERM, and the single-lane layout also keeps the pivot sequence.
@@ -628,6 +630,87 @@ __device__ void lu_factor(const Team& tm) {
   }
   for (int i = 0; i < NEQ; ++i) tm.perm(i) = i;
   for (int k = 0; k < NEQ; ++k) { const int p = tm.piv(k); if (p != k) { const int t = tm.perm(k); tm.perm(k) = tm.perm(p); tm.perm(p) = t; } }
+#elif TEAM > 32
+  // Block-per-cell teams: right-looking LU blocked in panels of LU_W columns, so that the block
+  // barriers are per panel, not per column.  Per panel: (a) the first warp factors the panel
+  // (pivot search in the panel column, swap of whole rows, 1/pivot, column scale and the rank-1
+  // updates of the remaining panel columns; warp synchronisation only); (b) the panel's block
+  // row right of it becomes U12 = L11^-1 A12 (unit-lower forward substitution, one column per
+  // lane); (c) the trailing matrix takes the rank-LU_W update A22 -= L21 U12, every element
+  // read and written once per panel.  The pivots are those of column-by-column partial pivoting
+  // (largest |a|, lowest row on ties): each panel column is fully updated before its search.
+  for (int i = tm.tl; i < NEQ; i += TEAM) tm.perm(i) = i;
+  __syncthreads();
+  for (int k0 = 0; k0 < NEQ; k0 += LU_W) {
+    const int kw = NEQ - k0 < LU_W ? NEQ - k0 : LU_W;
+    const int kend = k0 + kw;
+    if (tm.tl < 32) {
+      const int ln = tm.tl;
+      for (int k = k0; k < kend; ++k) {
+        long long best = -1;
+        int p = NEQ;
+        for (int i = k + ln; i < NEQ; i += 32) {
+          const long long v = abs_key(tm.A(i, k));
+          if (v > best) { best = v; p = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const long long vb = __shfl_xor_sync(0xffffffffu, best, o);
+          const int pb = __shfl_xor_sync(0xffffffffu, p, o);
+          if (vb > best || (vb == best && pb < p)) { best = vb; p = pb; }
+        }
+        if (p != k)
+          for (int j = ln; j < NEQ; j += 32) { const double t = tm.A(k, j); tm.A(k, j) = tm.A(p, j); tm.A(p, j) = t; }
+        __syncwarp();
+        const double inv = 1.0 / tm.A(k, k);
+        __syncwarp();  // every lane has read U_kk before lane 0 replaces it by its inverse
+        if (ln == 0) {
+          tm.invd(k) = inv;
+          if (p != k) { const int t = tm.perm(k); tm.perm(k) = tm.perm(p); tm.perm(p) = t; }
+        }
+        for (int i = k + 1 + ln; i < NEQ; i += 32) {
+          const double l = tm.A(i, k) * inv;
+          tm.A(i, k) = l;
+          for (int j = k + 1; j < kend; ++j) tm.A(i, j) -= l * tm.A(k, j);
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (kend < NEQ) {
+      // (b) U12 = L11^-1 A12
+      for (int j = kend + tm.tl; j < NEQ; j += TEAM) {
+        double u[LU_W];
+#pragma unroll
+        for (int r = 0; r < LU_W; ++r) {
+          if (r < kw) {
+            double v = tm.A(k0 + r, j);
+#pragma unroll
+            for (int q = 0; q < r; ++q) v -= tm.A(k0 + r, k0 + q) * u[q];
+            u[r] = v;
+            tm.A(k0 + r, j) = v;
+          }
+        }
+      }
+      __syncthreads();
+      // (c) A22 -= L21 U12
+      const int m = NEQ - kend;
+      const int tot = m * m;
+      const int qd = TEAM / m, rm = TEAM - qd * m;
+      int i = tm.tl / m, j = tm.tl - (tm.tl / m) * m;
+      for (int e = tm.tl; e < tot; e += TEAM) {
+        double v = tm.A(kend + i, kend + j);
+#pragma unroll
+        for (int q = 0; q < LU_W; ++q)
+          if (q < kw) v -= tm.A(kend + i, k0 + q) * tm.A(k0 + q, kend + j);
+        tm.A(kend + i, kend + j) = v;
+        i += qd;
+        j += rm;
+        if (j >= m) { j -= m; ++i; }
+      }
+      __syncthreads();
+    }
+  }
 #else
   // the composed permutation is built as the pivots are chosen (lane 0, after the row swap's
   // barrier), so no serial pass over the pivots is needed afterwards
@@ -647,19 +730,6 @@ __device__ void lu_factor(const Team& tm) {
       const int pb = __shfl_xor_sync(msk, p, o);
       if (vb > best || (vb == best && pb < p)) { best = vb; p = pb; }
     }
-#if TEAM > 32
-    {
-      long long* rv = reinterpret_cast<long long*>(&tm.base[OFF_RED]);
-      int* ri = reinterpret_cast<int*>(&tm.base[OFF_RED + 8]);
-      if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = p; }
-      __syncthreads();
-      best = rv[0];
-      p = ri[0];
-      for (int w = 1; w < TEAM / 32; ++w)
-        if (rv[w] > best || (rv[w] == best && ri[w] < p)) { best = rv[w]; p = ri[w]; }
-      __syncthreads();
-    }
-#endif
     if (p != k)
       for (int j = tm.tl; j < NEQ; j += TEAM) { const double t = tm.A(k, j); tm.A(k, j) = tm.A(p, j); tm.A(p, j) = t; }
     tsync();
