@@ -511,10 +511,12 @@ def prepare_inputs(m, synth, torch, np, dev, wl, cells=0):
 
 
 def forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, steps, warmup, rtol, atol,
-                tableau=0, clocks_index=None, world=1, plain=True, plain_runs=1):
+                tableau=0, clocks_index=None, world=1, plain=True, plain_runs=1, cost_order=False):
     """Times `steps` bench steps (each: restore inputs, flush L2, `splits` split steps, graph-
     captured when splits > 1) after `warmup` untimed ones; optionally the plain driver on the
-    same inputs.  Returns a dict of times (s), attempts per cell and the clock summary."""
+    same inputs.  cost_order: from the second split step on, the work queue hands out the cells
+    by decreasing attempts of the previous split step (chem_cost_order, inside the graph).
+    Returns a dict of times (s), attempts per cell and the clock summary."""
     n_cells = T0.shape[0]
     T, Y = T0.clone(), Y0.clone()
     h = torch.zeros(n_cells, dtype=torch.float64, device=dev)
@@ -535,13 +537,20 @@ def forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, steps, warmup, r
     def one_split(o=opts, w=ws):
         m.integrate(T, P, Y, dt, rtol=rtol, atol=atol, h=h, status=status, opts=o, workspace=w)
 
+    order = torch.arange(n_cells, dtype=torch.int32, device=dev)
+    ows = torch.empty(int(m._lib.chem_cost_order_workspace()) + 256, dtype=torch.uint8, device=dev)
+    ows = ows[(256 - ows.data_ptr() % 256) % 256:]
+    oopts = m.opts(attempts=att, tableau=tableau, order=order)
+
     if splits > 1:
         # consecutive split steps (h carried) captured once as a CUDA graph and replayed
         def splits_body():
             att_total.zero_()
-            for _ in range(splits):
-                one_split()
+            for sp in range(splits):
+                one_split(oopts if (cost_order and sp > 0) else opts)
                 att_total.add_(att)
+                if cost_order and sp + 1 < splits:
+                    m.cost_order(att, order, ows)
 
         restore()
         s_cap = torch.cuda.Stream()
@@ -602,7 +611,7 @@ def forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, steps, warmup, r
             pt.append(e0.elapsed_time(e1) * 1e-3)
         res["plain_s"] = min(pt)
         del pws
-    del ws, flush
+    del ws, flush, ows
     return res
 
 
@@ -707,7 +716,6 @@ def main():
         t0 = time.perf_counter()
         tuned = m.autotune(T0, P, Y0, dt)
         tuned["autotune_wall_s"] = time.perf_counter() - t0
-        tuned["sample_cells"] = min(n_cells, 4096)
 
     run = forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, args.steps, args.warmup,
                       args.rtol, args.atol, tableau=args.tableau, clocks_index=local,
@@ -745,6 +753,16 @@ def main():
 
     extra = {}
     full = not args.cells and world == 1
+    if full and not args.no_extra and splits > 1:
+        # the same workload with the cost-ordered queue (cells by decreasing attempts of the
+        # previous split step), against the index-order queue of the timed line
+        rc = forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, 2, 1, args.rtol,
+                         args.atol, tableau=args.tableau, clocks_index=local, plain=False,
+                         cost_order=True)
+        s_c = statistics.median(rc["times"])
+        extra["cost_ordered_queue"] = {"value": n_cells * splits / s_c, "unit": "cells/s",
+                                       "ms_per_step": s_c * 1e3, "speedup_over_index_order": sec / s_c,
+                                       "steps": 2}
     if full and not args.no_extra and wl == DEFAULT_WORKLOAD and args.tableau == 0:
         # the 53-species forward workload (one split step over 65,536 cells)
         wl2 = "ch4_53_fwd"

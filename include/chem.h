@@ -96,6 +96,10 @@ typedef struct {
   int32_t* attempts;   /* device [n_cells] out: step attempts per cell; NULL = not written */
   int32_t tableau;     /* method, CHEM_ROS4 (0, default) .. CHEM_RODAS4, or CHEM_RKF45; the step-size
                           controller uses err^(-1/order); the adjoint entry points need CHEM_ROS4 */
+  const int32_t* order; /* device [n_cells] (nullable): the persistent driver's work queue hands out
+                          the cells in this order -- a permutation of 0..n_cells-1, e.g. the
+                          cost order of chem_cost_order; entries outside [0, n_cells) are skipped.
+                          The results of a cell do not depend on the order. */
 } chem_int_opts;
 
 /* Parse a mechanism spec file (format: paper_2205_05681_gb300/synth.py docstring), build its
@@ -240,6 +244,18 @@ int chem_adjoint_noalloc(chem_mech_t mech, int64_t n_cells, const double* P, con
 int chem_eval_vjp(chem_mech_t mech, int64_t n_cells, const double* T, const double* P,
                   const double* n, const double* v, double* gy, double* gp, int64_t ld,
                   const double* lnA, void* stream);
+
+/* Cost-ordered work queue (load balancing of cells of uneven stiffness, after the paper's call
+ * for stiffness-based load balancing in Sec. 5): writes to order [n_cells] (device) a permutation
+ * of the cells by decreasing cost [n_cells] (device int32, e.g. the attempts of the previous split
+ * step from chem_int_opts.attempts), so that the most expensive cells start first and the tail of
+ * the persistent launch is short.  A counting sort over 1024 cost buckets (costs above 1023 share
+ * the top bucket); cells of equal cost come in no particular order.  workspace: device memory of
+ * chem_cost_order_workspace() bytes, 256-byte aligned.  Asynchronous on `stream`, no allocation,
+ * no host synchronisation (capturable in a CUDA graph). */
+size_t chem_cost_order_workspace(void);
+int chem_cost_order(chem_mech_t mech, int64_t n_cells, const int32_t* cost, int32_t* order,
+                    void* workspace, size_t ws_bytes, void* stream);
 
 /* Autotuner: picks the fastest kernel configuration (lanes per cell "team" -- from several
  * cells per warp (4, 8, 16 lanes) for small mechanisms up to a block of 256 lanes per cell -- and

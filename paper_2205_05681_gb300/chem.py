@@ -24,7 +24,8 @@ EXPORTS = ["chem_mech_load", "chem_mech_compile_only", "chem_mech_free", "chem_m
            "chem_mech_lnA", "chem_eval_source", "chem_eval_jacobian", "chem_integrate_workspace",
            "chem_integrate", "chem_integrate_host", "chem_kernel_config", "chem_autotune",
            "chem_tape_bytes", "chem_integrate_ckpt", "chem_adjoint_workspace", "chem_adjoint",
-           "chem_eval_vjp", "chem_adjoint_noalloc", "chem_fp64_probe", "chem_last_error"]
+           "chem_eval_vjp", "chem_adjoint_noalloc", "chem_fp64_probe", "chem_cost_order",
+           "chem_cost_order_workspace", "chem_last_error"]
 STATUS_TAPE_FULL = 5
 
 CACHE_DIR = os.environ.get("CHEM_CACHE_DIR", os.path.join(os.path.dirname(__file__), "_cache"))
@@ -43,7 +44,8 @@ class TapeStruct(C.Structure):
 class IntOpts(C.Structure):
     _fields_ = [("max_steps", C.c_int32), ("h_min", C.c_double), ("T_min", C.c_double),
                 ("mode", C.c_int32), ("team", C.c_int32), ("block", C.c_int32),
-                ("lnA", C.c_void_p), ("attempts", C.c_void_p), ("tableau", C.c_int32)]
+                ("lnA", C.c_void_p), ("attempts", C.c_void_p), ("tableau", C.c_int32),
+                ("order", C.c_void_p)]
 
 
 _lib = None
@@ -95,6 +97,9 @@ def library(build_if_missing: bool = True):
             lib.chem_adjoint_noalloc.argtypes = [vp, i64, vp, vp, vp, i64, C.POINTER(TapeStruct),
                                                  C.POINTER(IntOpts), vp, vp, vp, vp]
             lib.chem_fp64_probe.argtypes = [vp] + [C.POINTER(C.c_double)] * 3
+            lib.chem_cost_order_workspace.restype = C.c_size_t
+            lib.chem_cost_order_workspace.argtypes = []
+            lib.chem_cost_order.argtypes = [vp, i64, vp, vp, vp, C.c_size_t, vp]
             lib.chem_autotune.argtypes = [vp, i64, vp, vp, vp, i64, dbl, dbl, dbl, vp,
                                           C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                           C.POINTER(C.c_float)]
@@ -203,10 +208,26 @@ class Mechanism:
 
     # ------------------------------------------------------------------ integration
     def opts(self, mode=MODE_PERSISTENT, max_steps=0, h_min=0.0, T_min=0.0, team=0, block=0,
-             lnA=None, attempts=None, tableau=ROS4) -> IntOpts:
+             lnA=None, attempts=None, tableau=ROS4, order=None) -> IntOpts:
         return IntOpts(max_steps, h_min, T_min, mode, team, block,
                        None if lnA is None else lnA.data_ptr(),
-                       None if attempts is None else attempts.data_ptr(), int(tableau))
+                       None if attempts is None else attempts.data_ptr(), int(tableau),
+                       None if order is None else order.data_ptr())
+
+    def cost_order(self, cost, order=None, workspace=None, stream=None):
+        """Cells by decreasing cost (int32 [C] device) -> order int32 [C] (chem_cost_order)."""
+        import torch
+        Cn = cost.shape[0]
+        _req(cost, "cost", dtype=torch.int32, shape=(Cn,))
+        if order is None:
+            order = torch.empty(Cn, dtype=torch.int32, device=cost.device)
+        _req(order, "order", dtype=torch.int32, shape=(Cn,))
+        if workspace is None:
+            nb = int(self._lib.chem_cost_order_workspace())
+            workspace = torch.empty((nb + 255) // 256 * 256, dtype=torch.uint8, device=cost.device)
+        _check(self._lib.chem_cost_order(self._h, Cn, _ptr(cost), _ptr(order), _ptr(workspace),
+                                         workspace.numel(), _stream(stream)))
+        return order
 
     def integrate_workspace(self, n_cells: int, opts: Optional[IntOpts] = None) -> int:
         o = opts or self.opts()

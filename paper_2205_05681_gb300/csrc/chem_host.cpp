@@ -8,6 +8,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -655,7 +656,8 @@ struct Module {
   int team = 0, tpb = 0;
   CUmodule mod = nullptr;
   CUfunction f_source = nullptr, f_jac = nullptr, f_int = nullptr, f_pinit = nullptr, f_patt = nullptr,
-             f_pfin = nullptr, f_adj = nullptr, f_adjred = nullptr, f_vjp = nullptr;
+             f_pfin = nullptr, f_adj = nullptr, f_adjred = nullptr, f_vjp = nullptr, f_ohist = nullptr,
+             f_oscan = nullptr, f_oscat = nullptr;
   int smem = 0;          // dynamic shared memory per block
   int adj_smem = 0;      // ... of the adjoint / VJP kernels (0: not available for this config)
   int adj_occ = 0;
@@ -756,6 +758,9 @@ int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = fal
   CU_TRY(drv::cuModuleGetFunction(&mod->f_pinit, mod->mod, "chem_plain_init_k"));
   CU_TRY(drv::cuModuleGetFunction(&mod->f_patt, mod->mod, "chem_plain_attempt_k"));
   CU_TRY(drv::cuModuleGetFunction(&mod->f_pfin, mod->mod, "chem_plain_finish_k"));
+  CU_TRY(drv::cuModuleGetFunction(&mod->f_ohist, mod->mod, "chem_order_hist_k"));
+  CU_TRY(drv::cuModuleGetFunction(&mod->f_oscan, mod->mod, "chem_order_scan_k"));
+  CU_TRY(drv::cuModuleGetFunction(&mod->f_oscat, mod->mod, "chem_order_scatter_k"));
   CUdeviceptr slots_ptr;
   size_t slots_sz;
   CU_TRY(drv::cuModuleGetGlobal(&slots_ptr, &slots_sz, mod->mod, "chem_slots"));
@@ -1018,9 +1023,12 @@ int chem_integrate(chem_mech_t m, int64_t n_cells, double* T, const double* P, d
     int* tnacc = nullptr;
     double* th = nullptr;
     double* tck = nullptr;
-    int cap = 0, interval = 1;
+    int cap = 0, interval = 1, keep = 0;
+    const int32_t* order = o ? o->order : nullptr;
+    const unsigned* ocount = nullptr;
     void* args[] = {&nc, &T, (void*)&P, &Y, &l, &dt, &rtol, &atol, &h, &status, &att, (void*)&lnA,
-                    &max_steps, &h_min, &T_min, &q, &tnacc, &th, &tck, &cap, &interval};
+                    &max_steps, &h_min, &T_min, &q, &tnacc, &th, &tck, &cap, &interval,
+                    (void*)&order, (void*)&ocount, &keep};
     return launch(mod->f_int, grid_for(m, mod, n_cells), mod, stream, args);
   }
   if (mode != CHEM_MODE_PLAIN) return fail(CHEM_EARG, "unknown mode %d", mode);
@@ -1163,8 +1171,12 @@ int chem_integrate_ckpt(chem_mech_t m, int64_t n_cells, double* T, const double*
   long long nc = n_cells, l = ld;
   CUdeviceptr q = (CUdeviceptr)ws;
   CU_TRY(drv::cuMemsetD32Async(q, 0, 2, (CUstream)stream));
+  const int32_t* order = o ? o->order : nullptr;
+  const unsigned* ocount = nullptr;
+  int keep = 0;
   void* args[] = {&nc, &T, (void*)&P, &Y, &l, &dt, &rtol, &atol, &h, &status, &att, (void*)&lnA,
-                  &max_steps, &h_min, &T_min, &q, &tnacc, &th, &tck, &cap, &interval};
+                  &max_steps, &h_min, &T_min, &q, &tnacc, &th, &tck, &cap, &interval, (void*)&order,
+                  (void*)&ocount, &keep};
   return launch(mod->f_int, grid_for(m, mod, n_cells), mod, stream, args);
 }
 
@@ -1318,6 +1330,34 @@ int chem_eval_vjp(chem_mech_t m, int64_t n_cells, const double* T, const double*
   const int64_t tpb = teams_per_block(mod);
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_cells + tpb - 1) / tpb, (int64_t)m->n_sm * mod->adj_occ));
   CU_TRY(drv::cuLaunchKernel(mod->f_vjp, grid, 1, 1, mod->tpb, 1, 1, mod->adj_smem, (CUstream)stream, args, nullptr));
+  return 0;
+}
+
+size_t chem_cost_order_workspace(void) { return 256 + 2 * 1024 * sizeof(unsigned); }
+
+int chem_cost_order(chem_mech_t m, int64_t n_cells, const int32_t* cost, int32_t* order, void* ws, size_t ws_bytes,
+                    void* stream) {
+  if (!m) return fail(CHEM_EARG, "NULL mechanism");
+  if (n_cells < 0 || n_cells > INT32_MAX) return fail(CHEM_EARG, "n_cells out of range");
+  if (n_cells == 0) return 0;
+  if (!cost || !order) return fail(CHEM_EARG, "NULL array");
+  if (!ws || ws_bytes < chem_cost_order_workspace() || (((uintptr_t)ws) & 255))
+    return fail(CHEM_EWS, "cost-order workspace of %zu aligned bytes needed", chem_cost_order_workspace());
+  if (int rc = make_current(m)) return rc;
+  Module* mod;
+  if (int rc = resolve(m, nullptr, &mod)) return rc;
+  CUstream s = (CUstream)stream;
+  unsigned* bins = (unsigned*)ws;
+  unsigned* starts = bins + 1024;
+  CU_TRY(drv::cuMemsetD32Async((CUdeviceptr)bins, 0, 1024, s));
+  long long nc = n_cells;
+  const unsigned grid = (unsigned)((n_cells + 255) / 256);
+  void* ha[] = {&nc, (void*)&cost, &bins};
+  CU_TRY(drv::cuLaunchKernel(mod->f_ohist, grid, 1, 1, 256, 1, 1, 0, s, ha, nullptr));
+  void* sa[] = {&bins, &starts};
+  CU_TRY(drv::cuLaunchKernel(mod->f_oscan, 1, 1, 1, 1024, 1, 1, 0, s, sa, nullptr));
+  void* ca[] = {&nc, (void*)&cost, &starts, &order};
+  CU_TRY(drv::cuLaunchKernel(mod->f_oscat, grid, 1, 1, 256, 1, 1, 0, s, ca, nullptr));
   return 0;
 }
 

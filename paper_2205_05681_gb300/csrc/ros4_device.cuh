@@ -603,8 +603,6 @@ __device__ void eval_f_jac(const Team& tm, int oy, int of, double P, const doubl
 
 // ------------------------------------------------------------------------------ LU + solves
 
-#define LU_W 8  // panel width of the blocked LU of block-per-cell teams
-
 // In-place LU with partial pivoting of A (N x N): largest |a| in the column, lowest row on
 // ties.  1/U_kk replaces U_kk on the diagonal, the composed row permutation (row i of P A is row
 // perm[i] of A) goes to OFF_PERM, and the single-lane layout also keeps the pivot sequence.
@@ -630,87 +628,6 @@ __device__ void lu_factor(const Team& tm) {
   }
   for (int i = 0; i < NEQ; ++i) tm.perm(i) = i;
   for (int k = 0; k < NEQ; ++k) { const int p = tm.piv(k); if (p != k) { const int t = tm.perm(k); tm.perm(k) = tm.perm(p); tm.perm(p) = t; } }
-#elif TEAM > 32
-  // Block-per-cell teams: right-looking LU blocked in panels of LU_W columns, so that the block
-  // barriers are per panel, not per column.  Per panel: (a) the first warp factors the panel
-  // (pivot search in the panel column, swap of whole rows, 1/pivot, column scale and the rank-1
-  // updates of the remaining panel columns; warp synchronisation only); (b) the panel's block
-  // row right of it becomes U12 = L11^-1 A12 (unit-lower forward substitution, one column per
-  // lane); (c) the trailing matrix takes the rank-LU_W update A22 -= L21 U12, every element
-  // read and written once per panel.  The pivots are those of column-by-column partial pivoting
-  // (largest |a|, lowest row on ties): each panel column is fully updated before its search.
-  for (int i = tm.tl; i < NEQ; i += TEAM) tm.perm(i) = i;
-  __syncthreads();
-  for (int k0 = 0; k0 < NEQ; k0 += LU_W) {
-    const int kw = NEQ - k0 < LU_W ? NEQ - k0 : LU_W;
-    const int kend = k0 + kw;
-    if (tm.tl < 32) {
-      const int ln = tm.tl;
-      for (int k = k0; k < kend; ++k) {
-        long long best = -1;
-        int p = NEQ;
-        for (int i = k + ln; i < NEQ; i += 32) {
-          const long long v = abs_key(tm.A(i, k));
-          if (v > best) { best = v; p = i; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const long long vb = __shfl_xor_sync(0xffffffffu, best, o);
-          const int pb = __shfl_xor_sync(0xffffffffu, p, o);
-          if (vb > best || (vb == best && pb < p)) { best = vb; p = pb; }
-        }
-        if (p != k)
-          for (int j = ln; j < NEQ; j += 32) { const double t = tm.A(k, j); tm.A(k, j) = tm.A(p, j); tm.A(p, j) = t; }
-        __syncwarp();
-        const double inv = 1.0 / tm.A(k, k);
-        __syncwarp();  // every lane has read U_kk before lane 0 replaces it by its inverse
-        if (ln == 0) {
-          tm.invd(k) = inv;
-          if (p != k) { const int t = tm.perm(k); tm.perm(k) = tm.perm(p); tm.perm(p) = t; }
-        }
-        for (int i = k + 1 + ln; i < NEQ; i += 32) {
-          const double l = tm.A(i, k) * inv;
-          tm.A(i, k) = l;
-          for (int j = k + 1; j < kend; ++j) tm.A(i, j) -= l * tm.A(k, j);
-        }
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    if (kend < NEQ) {
-      // (b) U12 = L11^-1 A12
-      for (int j = kend + tm.tl; j < NEQ; j += TEAM) {
-        double u[LU_W];
-#pragma unroll
-        for (int r = 0; r < LU_W; ++r) {
-          if (r < kw) {
-            double v = tm.A(k0 + r, j);
-#pragma unroll
-            for (int q = 0; q < r; ++q) v -= tm.A(k0 + r, k0 + q) * u[q];
-            u[r] = v;
-            tm.A(k0 + r, j) = v;
-          }
-        }
-      }
-      __syncthreads();
-      // (c) A22 -= L21 U12
-      const int m = NEQ - kend;
-      const int tot = m * m;
-      const int qd = TEAM / m, rm = TEAM - qd * m;
-      int i = tm.tl / m, j = tm.tl - (tm.tl / m) * m;
-      for (int e = tm.tl; e < tot; e += TEAM) {
-        double v = tm.A(kend + i, kend + j);
-#pragma unroll
-        for (int q = 0; q < LU_W; ++q)
-          if (q < kw) v -= tm.A(kend + i, k0 + q) * tm.A(k0 + q, kend + j);
-        tm.A(kend + i, kend + j) = v;
-        i += qd;
-        j += rm;
-        if (j >= m) { j -= m; ++i; }
-      }
-      __syncthreads();
-    }
-  }
 #else
   // the composed permutation is built as the pivots are chosen (lane 0, after the row swap's
   // barrier), so no serial pass over the pivots is needed afterwards
@@ -730,6 +647,19 @@ __device__ void lu_factor(const Team& tm) {
       const int pb = __shfl_xor_sync(msk, p, o);
       if (vb > best || (vb == best && pb < p)) { best = vb; p = pb; }
     }
+#if TEAM > 32
+    {
+      long long* rv = reinterpret_cast<long long*>(&tm.base[OFF_RED]);
+      int* ri = reinterpret_cast<int*>(&tm.base[OFF_RED + 8]);
+      if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = p; }
+      __syncthreads();
+      best = rv[0];
+      p = ri[0];
+      for (int w = 1; w < TEAM / 32; ++w)
+        if (rv[w] > best || (rv[w] == best && ri[w] < p)) { best = rv[w]; p = ri[w]; }
+      __syncthreads();
+    }
+#endif
     if (p != k)
       for (int j = tm.tl; j < NEQ; j += TEAM) { const double t = tm.A(k, j); tm.A(k, j) = tm.A(p, j); tm.A(p, j) = t; }
     tsync();
@@ -1164,7 +1094,8 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
                  int* __restrict__ attempts_out, const double* __restrict__ lnA_ext,
                  int max_steps, double h_min, double T_min, unsigned long long* queue,
                  int* __restrict__ tape_nacc, double* __restrict__ tape_h, double* __restrict__ tape_ck,
-                 int tape_cap, int interval) {
+                 int tape_cap, int interval, const int* __restrict__ order,
+                 const unsigned int* __restrict__ order_count, int keep_failed) {
   extern __shared__ double smem[];
   const Team tm = make_team(smem);
   long long cell = -1;
@@ -1173,13 +1104,22 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
   c.done = true;
   c.acc = false;
   int nacc = 0;
-  // bounded: every iteration either retires a cell or makes an attempt (<= max_steps per cell)
+  // queue positions: n_cells, or the device-held length of the cell list `order`
+  const long long nq = order_count ? (long long)*order_count : n_cells;
+  // bounded: every iteration either retires a cell or makes an attempt (<= max_steps per cell),
+  // or consumes a queue position
   for (;;) {
     if (c.done) {
       long long nc = 0;
-      if (tm.tl == 0) nc = (long long)atomicAdd(queue, 1ULL);
+      if (tm.tl == 0) {
+        const long long q = (long long)atomicAdd(queue, 1ULL);
+        if (q >= nq) nc = n_cells;
+        else if (order) nc = (order[q] >= 0 && order[q] < n_cells) ? order[q] : -1;
+        else nc = q;
+      }
       cell = team_bcast_ll(tm, nc);
       if (cell >= n_cells) break;
+      if (cell < 0) continue;  // an invalid entry of the cell list: skipped
       Pc = P[cell];
       c.t = 0.0;
       c.h = h_io ? h_io[cell] : 0.0;
@@ -1221,7 +1161,9 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
     }
     if (c.done) {
       if (tm.tl == 0 && tape_nacc) tape_nacc[cell] = nacc;
-      store_cell(tm, cell, T, Y, ld);
+      // keep_failed: a cell that did not reach dt leaves its input state in place (a later launch
+      // integrates it again from the start)
+      if (!(keep_failed && c.status != ST_OK)) store_cell(tm, cell, T, Y, ld);
       if (tm.tl == 0) {
         if (h_io) h_io[cell] = c.h;
         if (status_out) status_out[cell] = c.status;
@@ -1230,6 +1172,45 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
       tsync();
     }
   }
+}
+
+// Cost-ordered work queue: a permutation of the cells by decreasing predicted cost (a counting
+// sort over CHEM_ORDER_BINS cost buckets: histogram, descending exclusive scan, scatter).  Cells of
+// equal cost are placed in no particular order.
+#define ORDER_BINS 1024
+extern "C" __global__ void chem_order_hist_k(long long n_cells, const int* __restrict__ cost,
+                                             unsigned int* __restrict__ bins) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const int v = cost[c];
+  atomicAdd(&bins[v < 0 ? 0 : (v >= ORDER_BINS ? ORDER_BINS - 1 : v)], 1u);
+}
+
+// one block of ORDER_BINS threads: starts[b] = number of cells in bins above b
+extern "C" __global__ void __launch_bounds__(ORDER_BINS) chem_order_scan_k(const unsigned int* __restrict__ bins,
+                                                                          unsigned int* __restrict__ starts) {
+  __shared__ unsigned int sh[ORDER_BINS];
+  const int t = threadIdx.x;
+  sh[t] = bins[ORDER_BINS - 1 - t];  // descending order of cost
+  __syncthreads();
+  for (int o = 1; o < ORDER_BINS; o <<= 1) {
+    const unsigned int v = t >= o ? sh[t - o] : 0u;
+    __syncthreads();
+    sh[t] += v;
+    __syncthreads();
+  }
+  // inclusive scan over descending bins; exclusive start of bin b = inclusive value of its predecessor
+  const int b = ORDER_BINS - 1 - t;
+  starts[b] = t > 0 ? sh[t - 1] : 0u;
+}
+
+extern "C" __global__ void chem_order_scatter_k(long long n_cells, const int* __restrict__ cost,
+                                                unsigned int* __restrict__ starts, int* __restrict__ order) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const int v = cost[c];
+  const unsigned int pos = atomicAdd(&starts[v < 0 ? 0 : (v >= ORDER_BINS ? ORDER_BINS - 1 : v)], 1u);
+  order[pos] = (int)c;
 }
 
 // Plain driver, one launch per step attempt over all cells.  Per-cell controller state lives

@@ -569,3 +569,42 @@ def test_interleaved_reaction_order(mech_dir, mech_path):
         d[r] = 1e-30j
         ref[r] = (v[0] @ om.source_cplx(y[0], st.P[0], lnA=om.lnA + d).imag) / 1e-30
     assert np.all(np.abs(gp[0] - ref) <= 1e-11 * (np.abs(ref) + 1e-3 * np.abs(ref).max()))
+
+
+def test_cost_ordered_queue(omech, mech_path):
+    """chem_cost_order returns a permutation of the cells by decreasing cost bucket, and a work
+    queue in that order gives every cell the result of the index-order queue (the order only
+    decides which team takes a cell when); the oracle on a sample."""
+    import torch
+    name = "ch4_53"
+    om = omech(name)
+    g = _bench_config_mech(mech_path, name)
+    n = 3000
+    st = states(name, n, WORK[name], 31)
+    T0, P, Y0 = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    att = torch.zeros(n, dtype=torch.int32, device=T0.device)
+    T, Y = T0.clone(), Y0.clone()
+    g.integrate(T, P, Y, 1e-6, opts=g.opts(attempts=att))
+    ref = (T.cpu().numpy(), Y.cpu().numpy(), att.cpu().numpy())
+    order = g.cost_order(att)
+    o = order.cpu().numpy()
+    assert np.array_equal(np.sort(o), np.arange(n))
+    c = np.minimum(ref[2][o], 1023)
+    assert np.all(np.diff(c) <= 0)
+    T, Y = T0.clone(), Y0.clone()
+    att2 = torch.zeros(n, dtype=torch.int32, device=T0.device)
+    g.integrate(T, P, Y, 1e-6, opts=g.opts(attempts=att2, order=order))
+    assert (att2.cpu().numpy() == ref[2]).mean() >= 0.99
+    assert np.allclose(T.cpu().numpy(), ref[0], rtol=1e-9, atol=0)
+    assert np.allclose(Y.cpu().numpy(), ref[1], rtol=1e-8, atol=1e-16)
+    idx = np.append(o[:20], o[-4:])  # the most and the least expensive cells
+
+    class Sub:
+        P = st.P[idx]
+
+    y0 = om.state_from_TY(st.T[idx], st.Y[idx])
+    _check_integration(om, Sub, y0, gpu_state(om, T, Y)[idx], att2.cpu().numpy()[idx], 1e-6,
+                       "cost-order")
+    # cost buckets above 1023 share the top bucket; negative costs the bottom one
+    cost = torch.tensor(np.array([5, 2000, -3, 1023, 7], dtype=np.int32), device=T0.device)
+    assert g.cost_order(cost).cpu().numpy().tolist()[2:] == [4, 0, 2]
