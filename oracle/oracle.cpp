@@ -561,12 +561,35 @@ static Tableau rkf45_fehlberg() {
   return t;
 }
 
+// ROS2 of Verwer, Spee, Blom & Hundsdorfer (1999), "A second-order Rosenbrock method applied to
+// photochemical dispersion problems": (I - g h W) k1 = f(y), (I - g h W) k2 = f(y + h k1) - 2 k1,
+// y1 = y + 3/2 h k1 + 1/2 h k2, g = 1 + 1/sqrt(2).  Second order for ANY matrix W (a W-method,
+// the class the paper names for reusing Jacobians and their factorisations), L-stable for this
+// g.  Error estimate: the difference to the first-order y + h k1, i.e. h/2 (k1 + k2).  In the
+// transformed variables u_i = g h k_i of the other methods: a21 = 1/g, c21 = -2/g,
+// m = (3/(2g), 1/(2g)), e = (1/(2g), 1/(2g)).
+static Tableau ros2_w() {
+  Tableau t{};
+  t.s = 2;
+  t.order = 2;
+  t.gamma = 1.0 + 1.0 / std::sqrt(2.0);
+  const double g = t.gamma;
+  t.a[1][0] = 1.0 / g;
+  t.c[1][0] = -2.0 / g;
+  t.m[0] = 1.5 / g;
+  t.m[1] = 0.5 / g;
+  t.e[0] = 0.5 / g;
+  t.e[1] = 0.5 / g;
+  return t;
+}
+
 static Tableau tableau_by_id(int id) {
   switch (id) {
     case 1: return ros3_sandu();
     case 2: return rodas3_sandu();
     case 3: return rodas4_hw();
     case 4: return rkf45_fehlberg();
+    case 5: return ros2_w();
     default: return ros4_hw();
   }
 }
@@ -618,8 +641,10 @@ void erk_step(const Sys& sys, const Tableau& tb, const S* y, double h, S* ynew, 
 
 // One ROS4 step of size h from y: ynew and the embedded error vector (an explicit tableau
 // takes the explicit step).
+// W (nullable): the matrix in place of J(y) (W-methods); NULL = the exact Jacobian at y.
 template <class S, class Sys>
-void ros4_step(const Sys& sys, const Tableau& tb, const S* y, double h, S* ynew, S* err) {
+void ros4_step(const Sys& sys, const Tableau& tb, const S* y, double h, S* ynew, S* err,
+               const double* W = nullptr) {
   if (tb.erk) {
     erk_step(sys, tb, y, h, ynew, err);
     return;
@@ -627,7 +652,10 @@ void ros4_step(const Sys& sys, const Tableau& tb, const S* y, double h, S* ynew,
   const int N = sys.n();
   std::vector<S> J(N * N), M(N * N), u(tb.s * N), Y(N), F(N);
   std::vector<int> piv(N);
-  sys.jac(y, J.data());
+  if (W)
+    for (int i = 0; i < N * N; ++i) J[i] = W[i];
+  else
+    sys.jac(y, J.data());
   for (int i = 0; i < N; ++i)
     for (int j = 0; j < N; ++j) M[i * N + j] = (i == j ? S(1.0 / (h * tb.gamma)) : S(0.0)) - J[i * N + j];
   lu_factor(N, M.data(), piv.data());
@@ -724,6 +752,68 @@ IntResult integrate_one(const Sys& sys, const Tableau& tb, double* y, double dt,
       for (int i = 0; i < N; ++i) y[i] = ynew[i];
       res.accepted++;
       if (accepted_h) accepted_h->push_back(hh);
+      if (reject_last) fac = std::min(fac, 1.0);
+      reject_last = false;
+      const double hnext = hh * fac;
+      if (last) { h = hh < h ? h : hnext; break; }
+      t += hh;
+      h = hnext;
+    } else {
+      res.rejected++;
+      reject_last = true;
+      h = hh * fac;
+    }
+  }
+  res.h_out = h;
+  return res;
+}
+
+// The W-method with Jacobian reuse (tableau ros2_w, or any other tableau taken as a W-method):
+// each cell carries a cache {W, h_W, age} across attempts and calls.  An attempt of size hh reuses
+// W (hence the factorisation of I/(g hh) - W) when h_W == hh and age < WAGE_MAX; otherwise it
+// evaluates J at the attempt's initial state, stores it as W with h_W = hh and age 0.  Every
+// accepted step ages the cache by one.  h_W <= 0 marks an empty cache.  Otherwise the controller
+// of integrate_one.
+constexpr int WAGE_MAX = 32;
+
+struct WCache {
+  double* W;   // N x N
+  double* h;   // h_W
+  int* age;
+};
+
+template <class Sys>
+IntResult integrate_w(const Sys& sys, const Tableau& tb, double* y, double dt, double h_in, const IntOpts& o,
+                      WCache wc, int* n_jac) {
+  IntResult res;
+  const int N = sys.n();
+  for (int i = 0; i < N; ++i)
+    if (!std::isfinite(y[i])) { res.status = NONFINITE; res.h_out = h_in; return res; }
+  std::vector<double> ynew(N), e(N);
+  double t = 0.0;
+  double h = h_in > 0 ? h_in : dt;
+  bool reject_last = false;
+  for (;;) {
+    if (res.attempts >= o.max_steps) { res.status = MAX_STEPS; break; }
+    if (h < o.h_min) { res.status = H_UNDERFLOW; break; }
+    const bool last = t + 1.0001 * h >= dt;
+    const double hh = last ? dt - t : h;
+    if (!(*wc.h == hh && *wc.age < WAGE_MAX)) {
+      sys.jac(y, wc.W);
+      *wc.h = hh;
+      *wc.age = 0;
+      ++*n_jac;
+    }
+    ros4_step(sys, tb, y, hh, ynew.data(), e.data(), wc.W);
+    res.attempts++;
+    double err = err_norm(N, y, ynew.data(), e.data(), o.rtol, o.atol);
+    bool finite = std::isfinite(err);
+    for (int i = 0; i < N && finite; ++i) finite = std::isfinite(ynew[i]);
+    double fac = finite ? std::min(6.0, std::max(0.2, 0.9 * std::pow(std::max(err, 1e-10), -1.0 / tb.order))) : 0.2;
+    if (finite && err <= 1.0) {
+      for (int i = 0; i < N; ++i) y[i] = ynew[i];
+      res.accepted++;
+      ++*wc.age;
       if (reject_last) fac = std::min(fac, 1.0);
       reject_last = false;
       const double hnext = hh * fac;
@@ -930,6 +1020,116 @@ int orc_integrate(void* hm, int n, double* y, const double* P, const double* lnA
   for (int t = 1; t < std::max(1, nthreads); ++t) th.emplace_back(work);
   work();
   for (auto& t : th) t.join();
+  return 0;
+}
+
+// Per-cell switching between the explicit RKF45 (tableau 4) and the Rosenbrock method `tab`
+// (the policy of the GPU path's per-cell method array): method[c] > 0 = integrate with RKF45
+// under at most that many attempts and, if the cell does not reach dt within them (attempt limit
+// or step-size underflow), integrate it again from its initial state and step size with the
+// Rosenbrock method; method[c] <= 0 = the Rosenbrock method.  Written back for the next call:
+// after an explicit success with a attempts, 4a + 8; after a Rosenbrock integration with a
+// attempts, 4a + 8 if dt * rho <= 3a, else 0, where rho = max_i sum_j |J_ij| w_j / w_i is the
+// Gershgorin bound of the Jacobian at the initial state scaled by the error weights
+// w = atol + rtol |y| (the explicit method's stability-limited steps, about dt * rho / 3, would not
+// outnumber the Rosenbrock attempts).  Cells below T_min or with a non-finite state keep their
+// method.  attempts and status are those of the run that finished the cell.
+int orc_integrate_auto(void* hm, int n, double* y, const double* P, const double* lnA, double dt, double rtol,
+                       double atol, double* h, int* status, int* attempts, int* method, int max_steps,
+                       double T_min, int nthreads, int tab) {
+  const Mech& m = *static_cast<Mech*>(hm);
+  const Tableau tr = tableau_by_id(tab), te = tableau_by_id(4);
+  std::atomic<int> next(0);
+  auto work = [&]() {
+    const int N = m.ns;
+    std::vector<double> y0(N), J(N * N);
+    for (int c; (c = next++) < n;) {
+      double* yc = y + (size_t)c * N;
+      const double h_in = h ? h[c] : 0.0;
+      IntResult r;
+      bool done = false;
+      if (T_min > 0 && yc[0] < T_min) {
+        r.status = SKIPPED;
+        r.h_out = h_in;
+        done = true;
+      }
+      for (int i = 0; i < N && !done; ++i)
+        if (!std::isfinite(yc[i])) { r.status = NONFINITE; r.h_out = h_in; done = true; }
+      ChemSys<double> sys{m, P[c], lnA};
+      if (!done && method[c] > 0) {
+        for (int i = 0; i < N; ++i) y0[i] = yc[i];
+        IntOpts o;
+        o.rtol = rtol; o.atol = atol; o.max_steps = std::min(max_steps, method[c]);
+        r = integrate_one(sys, te, yc, dt, h_in, o, nullptr);
+        if (r.status == OK) {
+          method[c] = 4 * r.attempts + 8;
+          done = true;
+        } else {
+          for (int i = 0; i < N; ++i) yc[i] = y0[i];
+        }
+      }
+      if (!done) {
+        sys.jac(yc, J.data());
+        double rho = 0.0;
+        for (int i = 0; i < N; ++i) {
+          double sum = 0.0;
+          for (int j = 0; j < N; ++j) sum += std::fabs(J[i * N + j]) * (atol + rtol * std::fabs(yc[j]));
+          rho = std::max(rho, sum / (atol + rtol * std::fabs(yc[i])));
+        }
+        IntOpts o;
+        o.rtol = rtol; o.atol = atol; o.max_steps = max_steps;
+        r = integrate_one(sys, tr, yc, dt, h_in, o, nullptr);
+        method[c] = (r.status == OK && dt * rho <= 3.0 * r.attempts) ? 4 * r.attempts + 8 : 0;
+      }
+      if (h) h[c] = r.h_out;
+      if (status) status[c] = r.status;
+      if (attempts) attempts[c] = r.attempts;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < std::max(1, nthreads); ++t) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+  return 0;
+}
+
+// The W-method with Jacobian reuse over n cells (see integrate_w); the caches Wc [n x N x N],
+// hW [n] and age [n] persist between calls (zero hW to empty them); n_jac [n] out: Jacobian
+// evaluations of this call.
+int orc_integrate_w(void* hm, int n, double* y, const double* P, const double* lnA, double dt, double rtol,
+                    double atol, double* h, int* status, int* attempts, int* n_jac, double* Wc, double* hW,
+                    int* age, int max_steps, int nthreads, int tab) {
+  const Mech& m = *static_cast<Mech*>(hm);
+  const Tableau tb = tableau_by_id(tab);
+  IntOpts o;
+  o.rtol = rtol; o.atol = atol; o.max_steps = max_steps;
+  std::atomic<int> next(0);
+  auto work = [&]() {
+    const int N = m.ns;
+    for (int c; (c = next++) < n;) {
+      ChemSys<double> sys{m, P[c], lnA};
+      int nj = 0;
+      WCache wc{Wc + (size_t)c * N * N, hW + c, age + c};
+      IntResult r = integrate_w(sys, tb, y + (size_t)c * N, dt, h ? h[c] : 0.0, o, wc, &nj);
+      if (h) h[c] = r.h_out;
+      if (status) status[c] = r.status;
+      if (attempts) attempts[c] = r.attempts;
+      if (n_jac) n_jac[c] = nj;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < std::max(1, nthreads); ++t) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+  return 0;
+}
+
+// One step of size h of the method `tab` with the matrix W (N x N) in place of the Jacobian.
+int orc_step_w(void* hm, const double* y, double P, const double* lnA, double h, const double* W, double* ynew,
+               double* err, int tab) {
+  const Mech& m = *static_cast<Mech*>(hm);
+  ChemSys<double> sys{m, P, lnA};
+  ros4_step(sys, tableau_by_id(tab), y, h, ynew, err, W);
   return 0;
 }
 

@@ -68,6 +68,13 @@ def _load():
             lib.orc_integrate.argtypes = [vp, C.c_int, _dp, _dp, vp, C.c_double, C.c_double,
                                           C.c_double, vp, vp, vp, vp, vp, C.c_int, C.c_double,
                                           C.c_double, C.c_int, C.c_int, C.c_int]
+            lib.orc_integrate_auto.argtypes = [vp, C.c_int, _dp, _dp, vp, C.c_double, C.c_double,
+                                               C.c_double, vp, vp, vp, _ip, C.c_int, C.c_double,
+                                               C.c_int, C.c_int]
+            lib.orc_integrate_w.argtypes = [vp, C.c_int, _dp, _dp, vp, C.c_double, C.c_double,
+                                            C.c_double, vp, vp, vp, vp, _dp, _dp, _ip, C.c_int,
+                                            C.c_int, C.c_int]
+            lib.orc_step_w.argtypes = [vp, _dp, C.c_double, vp, C.c_double, _dp, _dp, _dp, C.c_int]
             lib.orc_integrate_log.argtypes = [vp, _dp, C.c_double, vp, C.c_double, C.c_double,
                                               C.c_double, C.c_double, C.c_int, _dp, C.c_int,
                                               C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -87,6 +94,7 @@ def _f64(a):
 
 ROS4, ROS3, RODAS3, RODAS4 = 0, 1, 2, 3  # the Rosenbrock methods of Table T:solvers
 RKF45 = 4  # the explicit Runge-Kutta-Fehlberg 4(5) of the same table
+ROS2W = 5  # the second-order W-method ROS2 (Verwer et al. 1999), used with Jacobian reuse
 TABLEAUX = {"ROS4": ROS4, "ROS3": ROS3, "RODAS3": RODAS3, "RODAS4": RODAS4, "RKF45": RKF45}
 
 
@@ -248,6 +256,52 @@ class Mechanism:
                                 _ptr(att), _ptr(acc), _ptr(rej), max_steps, h_min, T_min,
                                 fixed_steps, threads, int(tableau))
         return y, {"h": hh, "status": st, "attempts": att, "accepted": acc, "rejected": rej}
+
+    def integrate_auto(self, y, P, dt, method, rtol=1e-6, atol=1e-10, h=None, lnA=None,
+                       max_steps=100000, T_min=0.0, threads: int = 1, tableau: int = ROS4):
+        """Per-cell switching between RKF45 and the Rosenbrock method `tableau` (see
+        orc_integrate_auto).  method: int32 [C], updated in place.  Returns (y, info)."""
+        y = _f64(np.atleast_2d(y)).copy()
+        n = y.shape[0]
+        P = _f64(np.broadcast_to(np.asarray(P, dtype=np.float64), (n,)))
+        hh = np.zeros(n) if h is None else _f64(h).copy()
+        st = np.zeros(n, dtype=np.int32)
+        att = np.zeros(n, dtype=np.int32)
+        assert method.dtype == np.int32 and method.flags["C_CONTIGUOUS"] and len(method) == n
+        lnA = None if lnA is None else _f64(lnA)
+        self._lib.orc_integrate_auto(self._h, n, y, P, _ptr(lnA), dt, rtol, atol, _ptr(hh),
+                                     _ptr(st), _ptr(att), method, max_steps, T_min, threads,
+                                     tableau)
+        return y, {"status": st, "attempts": att, "h": hh}
+
+    def w_cache(self, n):
+        """An empty Jacobian cache of the W-method for n cells: (W [n, N, N], h_W [n], age [n])."""
+        return (np.zeros((n, self.N, self.N)), np.zeros(n), np.zeros(n, dtype=np.int32))
+
+    def integrate_w(self, y, P, dt, cache, rtol=1e-6, atol=1e-10, h=None, lnA=None,
+                    max_steps=100000, threads: int = 1, tableau: int = ROS2W):
+        """The W-method with Jacobian reuse (orc_integrate_w); cache from w_cache(), updated in
+        place.  Returns (y, info) with info["n_jac"] the Jacobian evaluations per cell."""
+        y = _f64(np.atleast_2d(y)).copy()
+        n = y.shape[0]
+        P = _f64(np.broadcast_to(np.asarray(P, dtype=np.float64), (n,)))
+        hh = np.zeros(n) if h is None else _f64(h).copy()
+        st, att, nj = (np.zeros(n, dtype=np.int32) for _ in range(3))
+        W, hW, age = cache
+        assert W.flags["C_CONTIGUOUS"] and W.shape == (n, self.N, self.N)
+        lnA = None if lnA is None else _f64(lnA)
+        self._lib.orc_integrate_w(self._h, n, y, P, _ptr(lnA), dt, rtol, atol, _ptr(hh), _ptr(st),
+                                  _ptr(att), _ptr(nj), W.reshape(-1), hW, age, max_steps,
+                                  threads, tableau)
+        return y, {"status": st, "attempts": att, "h": hh, "n_jac": nj}
+
+    def step_w(self, y, P, h, W, lnA=None, tableau: int = ROS2W):
+        """One step of size h with the matrix W in place of the Jacobian: (y_new, error vector)."""
+        yn, e = np.zeros(self.N), np.zeros(self.N)
+        lnA = None if lnA is None else _f64(lnA)
+        self._lib.orc_step_w(self._h, _f64(y), float(P), _ptr(lnA), h, _f64(W).reshape(-1), yn, e,
+                             tableau)
+        return yn, e
 
     def integrate_log(self, y, P, dt, rtol=1e-6, atol=1e-10, h0=0.0, lnA=None, max_steps=100000):
         y = _f64(y).copy()
