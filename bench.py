@@ -43,9 +43,9 @@ METRIC = "cells integrated/s (ROS4, FP64, rtol 1e-6) vs plain GPU kernel; adjoin
 
 
 # stages and evaluations of f per attempt of each Rosenbrock method: (s, f evaluations incl. f(y))
-METHOD_SHAPE = {0: (4, 3), 1: (3, 2), 2: (4, 3), 3: (6, 6), 4: (6, 6)}  # (stages, f evaluations)
+METHOD_SHAPE = {0: (4, 3), 1: (3, 2), 2: (4, 3), 3: (6, 6), 4: (6, 6), 5: (2, 2)}  # (stages, f evaluations)
 EXPLICIT = {4}  # RKF45: no Jacobian, no factorisation, no solves
-METHODS = ["ROS4", "ROS3", "RODAS3", "RODAS4", "RKF45"]
+METHODS = ["ROS4", "ROS3", "RODAS3", "RODAS4", "RKF45", "ROS2W"]
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one chem_integrate_k launch on the
@@ -383,10 +383,15 @@ def workload_config(wl, args, world):
     spec = read_spec_counts(synth.mechanism_file(mech_name, MECH_DIR))
     if args.cells:
         n_cells = min(n_cells, args.cells)
+    if getattr(args, "splits", 0):
+        splits = args.splits
+    method = METHODS[args.tableau]
+    if getattr(args, "switching", ""):
+        method = "per-cell %s / %s" % ({"rkf45": "RKF45", "w": "ROS2W"}[args.switching], method)
     return {"workload": wl, "mechanism": mech_name, "species": spec["ns"],
             "reactions": len(spec["reactions"]), "cells": n_cells, "recipe": recipe,
             "state_seed": seed, "dt_s": dt, "split_steps_per_step": splits,
-            "method": METHODS[args.tableau], "cuda_graph": splits > 1, "rtol": args.rtol,
+            "method": method, "cuda_graph": splits > 1, "rtol": args.rtol,
             "atol": args.atol, "l2": "flushed (512 MiB write) between steps",
             "parallelism": "replicas" if world > 1 else "single"}
 
@@ -511,19 +516,30 @@ def prepare_inputs(m, synth, torch, np, dev, wl, cells=0):
 
 
 def forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, steps, warmup, rtol, atol,
-                tableau=0, clocks_index=None, world=1, plain=True, plain_runs=1, cost_order=False):
+                tableau=0, clocks_index=None, world=1, plain=True, plain_runs=1, cost_order=False,
+                switching=False, light_precapture=False):
     """Times `steps` bench steps (each: restore inputs, flush L2, `splits` split steps, graph-
     captured when splits > 1) after `warmup` untimed ones; optionally the plain driver on the
     same inputs.  cost_order: from the second split step on, the work queue hands out the cells
     by decreasing attempts of the previous split step (chem_cost_order, inside the graph).
-    Returns a dict of times (s), attempts per cell and the clock summary."""
+    switching: per-cell switching between RKF45 and the Rosenbrock method, the method array
+    carried from split step to split step (reset with the inputs).  light_precapture: the
+    untimed run before graph capture (which loads every module the graph launches) integrates
+    only the first 256 cells.  Returns a dict of times (s), attempts per cell, the cells that
+    ended on the explicit method, and the clock summary."""
     n_cells = T0.shape[0]
     T, Y = T0.clone(), Y0.clone()
     h = torch.zeros(n_cells, dtype=torch.float64, device=dev)
     status = torch.zeros(n_cells, dtype=torch.int32, device=dev)
     att = torch.zeros(n_cells, dtype=torch.int32, device=dev)
     att_total = torch.zeros(n_cells, dtype=torch.int32, device=dev)
-    opts = m.opts(attempts=att, tableau=tableau)
+    meth = torch.zeros(n_cells, dtype=torch.int32, device=dev)
+    # the W-method's factorisation cache (the W-method itself, or the W-method as the switching
+    # alternative)
+    alt = 5 if switching == "w" else 4
+    jc = m.jac_cache(n_cells, device=dev) if (tableau == 5 or alt == 5) else None
+    opts = m.opts(attempts=att, tableau=tableau, cell_method=meth if switching else None,
+                  jac_cache=jc, alt_tableau=alt if switching else 0)
     ws = m.workspace(n_cells, opts, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -532,6 +548,9 @@ def forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, steps, warmup, r
         T.copy_(T0)
         Y.copy_(Y0)
         h.zero_()
+        meth.zero_()
+        if jc is not None:
+            jc.zero_()
         flush.fill_(1.0)  # evict the inputs from L2 (512 MiB > 129 MB)
 
     def one_split(o=opts, w=ws):
@@ -540,7 +559,9 @@ def forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, steps, warmup, r
     order = torch.arange(n_cells, dtype=torch.int32, device=dev)
     ows = torch.empty(int(m._lib.chem_cost_order_workspace()) + 256, dtype=torch.uint8, device=dev)
     ows = ows[(256 - ows.data_ptr() % 256) % 256:]
-    oopts = m.opts(attempts=att, tableau=tableau, order=order)
+    oopts = m.opts(attempts=att, tableau=tableau, order=order,
+                   cell_method=meth if switching else None, jac_cache=jc,
+                   alt_tableau=alt if switching else 0)
 
     if splits > 1:
         # consecutive split steps (h carried) captured once as a CUDA graph and replayed
@@ -556,7 +577,22 @@ def forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, steps, warmup, r
         s_cap = torch.cuda.Stream()
         s_cap.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s_cap):
-            splits_body()  # eager run on the capture stream before capture
+            if light_precapture:  # load the modules on a few cells
+                k = min(256, n_cells)
+                Tk, Pk, Yk = T0[:k].clone(), P[:k].clone(), Y0[:, :k].contiguous()
+                mk = torch.zeros(k, dtype=torch.int32, device=dev)
+                jk = m.jac_cache(k, device=dev) if jc is not None else None
+                ok = m.opts(tableau=tableau, cell_method=mk if switching else None, jac_cache=jk,
+                            alt_tableau=alt if switching else 0)
+                m.integrate(Tk, Pk, Yk, dt, rtol=rtol, atol=atol, opts=ok,
+                            workspace=m.workspace(k, ok, device=dev))
+                if switching:  # and the alternative method's module
+                    mk.fill_(64)
+                    m.integrate(Tk, Pk, Yk, dt, rtol=rtol, atol=atol, opts=ok,
+                                workspace=m.workspace(k, ok, device=dev))
+                m.cost_order(att[:k].contiguous())
+            else:
+                splits_body()  # eager run on the capture stream before capture
         torch.cuda.current_stream().wait_stream(s_cap)
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
@@ -566,6 +602,15 @@ def forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, steps, warmup, r
         def one_step():
             graph.replay()
     else:
+        if switching:  # load the alternative method's module before timing
+            mk = torch.full((min(256, n_cells),), 64, dtype=torch.int32, device=dev)
+            k = mk.shape[0]
+            jk = m.jac_cache(k, device=dev) if jc is not None else None
+            ok = m.opts(tableau=tableau, cell_method=mk, jac_cache=jk,
+                        alt_tableau=alt if switching else 0)
+            m.integrate(T0[:k].clone(), P[:k].clone(), Y0[:, :k].contiguous(), dt, rtol=rtol,
+                        atol=atol, opts=ok, workspace=m.workspace(k, ok, device=dev))
+
         def one_step():
             one_split()
             att_total.copy_(att)
@@ -592,7 +637,8 @@ def forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, steps, warmup, r
     if world > 1:
         dist.barrier()
     res = {"times": times, "attempts": att_total.cpu().numpy(),
-           "ok_cells": int((status == 0).sum().item()), "clocks": clk.summary()}
+           "ok_cells": int((status == 0).sum().item()), "clocks": clk.summary(),
+           "explicit_cells": int((meth > 0).sum().item()) if switching else 0}
     if plain:
         # the plain one-launch-per-attempt driver on the same inputs (split steps run eagerly: its
         # host polling cannot be captured in a graph); one run, its kernels are already loaded
@@ -611,7 +657,7 @@ def forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, steps, warmup, r
             pt.append(e0.elapsed_time(e1) * 1e-3)
         res["plain_s"] = min(pt)
         del pws
-    del ws, flush, ows
+    del ws, flush, ows, meth, jc
     return res
 
 
@@ -640,7 +686,10 @@ def roofline(spec, tableau, total_attempts, sec, probe, dgemm, sm_mhz, n_sm, wl,
             "traffic_unit": "bytes per launch (one split step)",
             "algorithmic_bytes_per_launch": int(8 * n_cells * (2 * (N + 1) + 3)),
             "kernel": "chem_integrate_k", "launches": launches,
-            "flops_per_attempt": fl, "transcendentals_per_attempt": trans}
+            "flops_per_attempt": fl, "transcendentals_per_attempt": trans,
+            "note": ("W-method: the Jacobian and factorisation are counted on every attempt, "
+                     "an upper bound (attempts that reuse the cached factorisation skip them)"
+                     if tableau == 5 else None)}
 
 
 def attempts_summary(a, ok):
@@ -670,9 +719,17 @@ def main():
     ap.add_argument("--tape-capacity", type=int, default=4096, help="adjoint workloads: steps/cell")
     ap.add_argument("--interval", type=int, default=16, help="adjoint workloads: checkpoint interval")
     ap.add_argument("--tableau", type=int, default=0,
-                    help="method: 0 ROS4 (default), 1 ROS3, 2 RODAS3, 3 RODAS4, 4 RKF45 (explicit)")
+                    help="method: 0 ROS4 (default), 1 ROS3, 2 RODAS3, 3 RODAS4, 4 RKF45 (explicit), "
+                         "5 ROS2W (W-method with factorisation reuse)")
     ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--atol", type=float, default=1e-10)
+    ap.add_argument("--splits", type=int, default=0,
+                    help="override the workload's split steps per bench step (graph-captured)")
+    ap.add_argument("--switching", default="", choices=["", "rkf45", "w"],
+                    help="per-cell switching on the timed leg between the Rosenbrock method and "
+                         "RKF45 (stiffness rule) or the W-method ROS2 (quiescent cells)")
+    ap.add_argument("--cost-order", action="store_true",
+                    help="cost-ordered work queue on the timed leg (split steps after the first)")
     ap.add_argument("--work-precision", action="store_true",
                     help="error vs time of the four Rosenbrock methods over tolerances 1e-4..1e-12")
     args = ap.parse_args()
@@ -704,6 +761,8 @@ def main():
             print(json.dumps(line), flush=True)
         return 0
     mech_name, n_all, recipe, seed, dt, splits = synth.WORKLOADS[wl]
+    if args.splits:
+        splits = args.splits
     path = synth.mechanism_file(mech_name, MECH_DIR + ("" if world == 1 else "_r%d" % rank))
     t0 = time.perf_counter()
     m = chem.Mechanism(path, team=args.team, block=args.block)
@@ -719,7 +778,8 @@ def main():
 
     run = forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, args.steps, args.warmup,
                       args.rtol, args.atol, tableau=args.tableau, clocks_index=local,
-                      world=world, plain=not args.no_plain)
+                      world=world, plain=not args.no_plain, switching=args.switching,
+                      cost_order=args.cost_order)
     sec = reduce_max_seconds(sum(run["times"]) / len(run["times"]), world, dev)
     value = whole_job_value(n_cells, splits, world, sec)
     attempts = run["attempts"]
@@ -753,16 +813,21 @@ def main():
 
     extra = {}
     full = not args.cells and world == 1
-    if full and not args.no_extra and splits > 1:
-        # the same workload with the cost-ordered queue (cells by decreasing attempts of the
-        # previous split step), against the index-order queue of the timed line
-        rc = forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, 2, 1, args.rtol,
-                         args.atol, tableau=args.tableau, clocks_index=local, plain=False,
-                         cost_order=True)
-        s_c = statistics.median(rc["times"])
-        extra["cost_ordered_queue"] = {"value": n_cells * splits / s_c, "unit": "cells/s",
-                                       "ms_per_step": s_c * 1e3, "speedup_over_index_order": sec / s_c,
-                                       "steps": 2}
+    if full and not args.no_extra and splits > 1 and not (args.switching or args.cost_order):
+        if args.tableau < 4:
+            # quiescent cells moved to the W-method, whose factorisation serves their next split
+            # steps (stiffness-aware switching; ROS4 keeps the reacting cells)
+            rs = forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, 1, 0, args.rtol,
+                             args.atol, tableau=args.tableau, clocks_index=local, plain=False,
+                             switching="w", light_precapture=True)
+            s_s = statistics.median(rs["times"])
+            extra["method_switching"] = {"alternative": "ROS2W with factorisation reuse",
+                                         "value": n_cells * splits / s_s, "unit": "cells/s",
+                                         "ms_per_step": s_s * 1e3,
+                                         "speedup_over_single_method": sec / s_s,
+                                         "cells_on_alternative_at_end": rs["explicit_cells"],
+                                         "attempts_mean": float(rs["attempts"].mean()), "steps": 1,
+                                         "ok_cells": rs["ok_cells"]}
     if full and not args.no_extra and wl == DEFAULT_WORKLOAD and args.tableau == 0:
         # the 53-species forward workload (one split step over 65,536 cells)
         wl2 = "ch4_53_fwd"

@@ -82,6 +82,13 @@ typedef struct {
  * difference to the fourth-order one, controller exponent 1/5).  For non-stiff cells only: on
  * stiff chemistry its stable step sizes are tiny and cells end with CHEM_STATUS_MAX_STEPS. */
 #define CHEM_RKF45 4
+/* A W-method (the class the paper names, Sec. 2.3 and Conclusions, for reusing Jacobians and
+ * their factorisations): ROS2 of Verwer, Spee, Blom & Hundsdorfer (1999), 2 stages, second order
+ * for any matrix W in place of the Jacobian, L-stable (gamma = 1 + 1/sqrt(2)), error estimate
+ * against the first-order solution (controller exponent 1/2).  With chem_int_opts.jac_cache the
+ * factorisation of I/(gamma h) - W is reused across attempts and calls while the step size is
+ * unchanged; without it every attempt evaluates and factorises the Jacobian. */
+#define CHEM_ROS2W 5
 
 /* Options for chem_integrate (NULL = defaults shown). */
 typedef struct {
@@ -94,12 +101,38 @@ typedef struct {
   const double* lnA;   /* device [Nr]: ln of the pre-exponential factors (SI units; for falloff
                           reactions the high-pressure limit); NULL = the mechanism's values */
   int32_t* attempts;   /* device [n_cells] out: step attempts per cell; NULL = not written */
-  int32_t tableau;     /* method, CHEM_ROS4 (0, default) .. CHEM_RODAS4, or CHEM_RKF45; the step-size
+  int32_t tableau;     /* method, CHEM_ROS4 (0, default) .. CHEM_RODAS4, CHEM_RKF45 or CHEM_ROS2W; the step-size
                           controller uses err^(-1/order); the adjoint entry points need CHEM_ROS4 */
   const int32_t* order; /* device [n_cells] (nullable): the persistent driver's work queue hands out
                           the cells in this order -- a permutation of 0..n_cells-1, e.g. the
                           cost order of chem_cost_order; entries outside [0, n_cells) are skipped.
                           The results of a cell do not depend on the order. */
+  int32_t* cell_method; /* device [n_cells] in/out (nullable): per-cell switching between the
+                          explicit RKF45 and the Rosenbrock method `tableau` (persistent mode;
+                          workspace per chem_integrate_workspace).  In: > 0 = integrate the cell
+                          with RKF45 under at most that many attempts, falling back to the
+                          Rosenbrock method from the cell's initial state if it does not reach
+                          dt within them; <= 0 = the Rosenbrock method.  Out: the choice for the
+                          next call -- after RKF45 succeeded with a attempts, 4a + 8; after a
+                          Rosenbrock integration with a attempts, 4a + 8 if dt * rho <= 3a
+                          (rho = max_i sum_j |J_ij| w_j / w_i at the first attempt, w = atol +
+                          rtol |y|: the explicit method's stability-limited steps would not
+                          outnumber the Rosenbrock attempts), else 0.  Start from zeros.
+                          attempts/status report the run that finished the cell. */
+  double* jac_cache;    /* device, chem_jac_cache_bytes(n_cells) bytes, 8-byte aligned (nullable;
+                          only with CHEM_ROS2W, persistent mode): per cell the factorised matrix
+                          I/(gamma h) - W of the W-method, the step size it was built for and its
+                          age, kept between attempts and between calls.  An attempt of size h reuses
+                          it (no Jacobian, no factorisation) when it was built for exactly h and has
+                          aged fewer than 32 accepted steps; otherwise it evaluates the Jacobian at
+                          the attempt's state, factorises and stores.  Zero it before the first call
+                          (an all-zero cache is empty); keep it with the cells between calls. */
+  int32_t alt_tableau;  /* the alternative method of cell_method switching: 0 or CHEM_RKF45 (the
+                          stiffness rule above), or CHEM_ROS2W (needs jac_cache): a cell whose
+                          Rosenbrock integration took a single attempt (quiescent, e.g. near
+                          equilibrium) runs the W-method on the next call with budget 12, reusing
+                          its cached factorisation across calls; the Rosenbrock launch empties the
+                          cache of the cells it integrates. */
 } chem_int_opts;
 
 /* Parse a mechanism spec file (format: paper_2205_05681_gb300/synth.py docstring), build its
@@ -245,8 +278,12 @@ int chem_eval_vjp(chem_mech_t mech, int64_t n_cells, const double* T, const doub
                   const double* n, const double* v, double* gy, double* gp, int64_t ld,
                   const double* lnA, void* stream);
 
+/* Bytes of the W-method factorisation cache of n_cells cells (chem_int_opts.jac_cache):
+ * n_cells x (Ns^2 + 2 ceil(Ns/2) + 2) doubles. */
+size_t chem_jac_cache_bytes(chem_mech_t mech, int64_t n_cells);
+
 /* Cost-ordered work queue (load balancing of cells of uneven stiffness, after the paper's call
- * for stiffness-based load balancing in Sec. 5): writes to order [n_cells] (device) a permutation
+ * for stiffness-based load balancing in its Conclusions, Sec. 6): writes to order [n_cells] (device) a permutation
  * of the cells by decreasing cost [n_cells] (device int32, e.g. the attempts of the previous split
  * step from chem_int_opts.attempts), so that the most expensive cells start first and the tail of
  * the persistent launch is short.  A counting sort over 1024 cost buckets (costs above 1023 share

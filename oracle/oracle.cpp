@@ -1034,11 +1034,14 @@ int orc_integrate(void* hm, int n, double* y, const double* P, const double* lnA
 // w = atol + rtol |y| (the explicit method's stability-limited steps, about dt * rho / 3, would not
 // outnumber the Rosenbrock attempts).  Cells below T_min or with a non-finite state keep their
 // method.  attempts and status are those of the run that finished the cell.
+// alt = 5 takes the W-method (with the caches Wc, hW, age of orc_integrate_w) as the alternative:
+// a cell goes to it after a single-attempt Rosenbrock integration (budget 12), and every
+// Rosenbrock integration empties the cell's cache.
 int orc_integrate_auto(void* hm, int n, double* y, const double* P, const double* lnA, double dt, double rtol,
                        double atol, double* h, int* status, int* attempts, int* method, int max_steps,
-                       double T_min, int nthreads, int tab) {
+                       double T_min, int nthreads, int tab, int alt, double* Wc, double* hW, int* wage) {
   const Mech& m = *static_cast<Mech*>(hm);
-  const Tableau tr = tableau_by_id(tab), te = tableau_by_id(4);
+  const Tableau tr = tableau_by_id(tab), te = tableau_by_id(alt == 5 ? 5 : 4);
   std::atomic<int> next(0);
   auto work = [&]() {
     const int N = m.ns;
@@ -1060,7 +1063,13 @@ int orc_integrate_auto(void* hm, int n, double* y, const double* P, const double
         for (int i = 0; i < N; ++i) y0[i] = yc[i];
         IntOpts o;
         o.rtol = rtol; o.atol = atol; o.max_steps = std::min(max_steps, method[c]);
-        r = integrate_one(sys, te, yc, dt, h_in, o, nullptr);
+        if (alt == 5) {
+          int nj = 0;
+          WCache wc{Wc + (size_t)c * N * N, hW + c, wage + c};
+          r = integrate_w(sys, te, yc, dt, h_in, o, wc, &nj);
+        } else {
+          r = integrate_one(sys, te, yc, dt, h_in, o, nullptr);
+        }
         if (r.status == OK) {
           method[c] = 4 * r.attempts + 8;
           done = true;
@@ -1079,7 +1088,12 @@ int orc_integrate_auto(void* hm, int n, double* y, const double* P, const double
         IntOpts o;
         o.rtol = rtol; o.atol = atol; o.max_steps = max_steps;
         r = integrate_one(sys, tr, yc, dt, h_in, o, nullptr);
-        method[c] = (r.status == OK && dt * rho <= 3.0 * r.attempts) ? 4 * r.attempts + 8 : 0;
+        if (alt == 5) {
+          method[c] = (r.status == OK && r.attempts == 1) ? 12 : 0;
+          hW[c] = 0.0;
+        } else {
+          method[c] = (r.status == OK && dt * rho <= 3.0 * r.attempts) ? 4 * r.attempts + 8 : 0;
+        }
       }
       if (h) h[c] = r.h_out;
       if (status) status[c] = r.status;

@@ -70,7 +70,7 @@ def _load():
                                           C.c_double, C.c_int, C.c_int, C.c_int]
             lib.orc_integrate_auto.argtypes = [vp, C.c_int, _dp, _dp, vp, C.c_double, C.c_double,
                                                C.c_double, vp, vp, vp, _ip, C.c_int, C.c_double,
-                                               C.c_int, C.c_int]
+                                               C.c_int, C.c_int, C.c_int, vp, vp, vp]
             lib.orc_integrate_w.argtypes = [vp, C.c_int, _dp, _dp, vp, C.c_double, C.c_double,
                                             C.c_double, vp, vp, vp, vp, _dp, _dp, _ip, C.c_int,
                                             C.c_int, C.c_int]
@@ -258,9 +258,11 @@ class Mechanism:
         return y, {"h": hh, "status": st, "attempts": att, "accepted": acc, "rejected": rej}
 
     def integrate_auto(self, y, P, dt, method, rtol=1e-6, atol=1e-10, h=None, lnA=None,
-                       max_steps=100000, T_min=0.0, threads: int = 1, tableau: int = ROS4):
-        """Per-cell switching between RKF45 and the Rosenbrock method `tableau` (see
-        orc_integrate_auto).  method: int32 [C], updated in place.  Returns (y, info)."""
+                       max_steps=100000, T_min=0.0, threads: int = 1, tableau: int = ROS4,
+                       alt: int = RKF45, cache=None):
+        """Per-cell switching between the alternative method `alt` (RKF45, or ROS2W with `cache`
+        from w_cache()) and the Rosenbrock method `tableau` (see orc_integrate_auto).
+        method: int32 [C], updated in place.  Returns (y, info)."""
         y = _f64(np.atleast_2d(y)).copy()
         n = y.shape[0]
         P = _f64(np.broadcast_to(np.asarray(P, dtype=np.float64), (n,)))
@@ -269,9 +271,12 @@ class Mechanism:
         att = np.zeros(n, dtype=np.int32)
         assert method.dtype == np.int32 and method.flags["C_CONTIGUOUS"] and len(method) == n
         lnA = None if lnA is None else _f64(lnA)
+        W, hW, age = cache if cache is not None else (None, None, None)
+        if alt == ROS2W:
+            assert cache is not None and W.shape == (n, self.N, self.N)
         self._lib.orc_integrate_auto(self._h, n, y, P, _ptr(lnA), dt, rtol, atol, _ptr(hh),
                                      _ptr(st), _ptr(att), method, max_steps, T_min, threads,
-                                     tableau)
+                                     tableau, alt, _ptr(W), _ptr(hW), _ptr(age))
         return y, {"status": st, "attempts": att, "h": hh}
 
     def w_cache(self, n):

@@ -25,7 +25,7 @@ EXPORTS = ["chem_mech_load", "chem_mech_compile_only", "chem_mech_free", "chem_m
            "chem_integrate", "chem_integrate_host", "chem_kernel_config", "chem_autotune",
            "chem_tape_bytes", "chem_integrate_ckpt", "chem_adjoint_workspace", "chem_adjoint",
            "chem_eval_vjp", "chem_adjoint_noalloc", "chem_fp64_probe", "chem_cost_order",
-           "chem_cost_order_workspace", "chem_last_error"]
+           "chem_cost_order_workspace", "chem_jac_cache_bytes", "chem_last_error"]
 STATUS_TAPE_FULL = 5
 
 CACHE_DIR = os.environ.get("CHEM_CACHE_DIR", os.path.join(os.path.dirname(__file__), "_cache"))
@@ -45,7 +45,8 @@ class IntOpts(C.Structure):
     _fields_ = [("max_steps", C.c_int32), ("h_min", C.c_double), ("T_min", C.c_double),
                 ("mode", C.c_int32), ("team", C.c_int32), ("block", C.c_int32),
                 ("lnA", C.c_void_p), ("attempts", C.c_void_p), ("tableau", C.c_int32),
-                ("order", C.c_void_p)]
+                ("order", C.c_void_p), ("cell_method", C.c_void_p),
+                ("jac_cache", C.c_void_p), ("alt_tableau", C.c_int32)]
 
 
 _lib = None
@@ -100,6 +101,8 @@ def library(build_if_missing: bool = True):
             lib.chem_cost_order_workspace.restype = C.c_size_t
             lib.chem_cost_order_workspace.argtypes = []
             lib.chem_cost_order.argtypes = [vp, i64, vp, vp, vp, C.c_size_t, vp]
+            lib.chem_jac_cache_bytes.restype = C.c_size_t
+            lib.chem_jac_cache_bytes.argtypes = [vp, i64]
             lib.chem_autotune.argtypes = [vp, i64, vp, vp, vp, i64, dbl, dbl, dbl, vp,
                                           C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                           C.POINTER(C.c_float)]
@@ -114,6 +117,7 @@ def _check(rc: int):
 
 ROS4, ROS3, RODAS3, RODAS4 = 0, 1, 2, 3  # Rosenbrock methods (CHEM_ROS4 ...)
 RKF45 = 4  # explicit Runge-Kutta-Fehlberg 4(5) (CHEM_RKF45), for non-stiff cells
+ROS2W = 5  # the W-method ROS2 (CHEM_ROS2W), with a factorisation cache (jac_cache)
 
 
 def compile_only(spec_path: str, team: int = 0, block: int = 0, cache_dir: Optional[str] = None,
@@ -208,11 +212,20 @@ class Mechanism:
 
     # ------------------------------------------------------------------ integration
     def opts(self, mode=MODE_PERSISTENT, max_steps=0, h_min=0.0, T_min=0.0, team=0, block=0,
-             lnA=None, attempts=None, tableau=ROS4, order=None) -> IntOpts:
+             lnA=None, attempts=None, tableau=ROS4, order=None, cell_method=None,
+             jac_cache=None, alt_tableau=0) -> IntOpts:
         return IntOpts(max_steps, h_min, T_min, mode, team, block,
                        None if lnA is None else lnA.data_ptr(),
                        None if attempts is None else attempts.data_ptr(), int(tableau),
-                       None if order is None else order.data_ptr())
+                       None if order is None else order.data_ptr(),
+                       None if cell_method is None else cell_method.data_ptr(),
+                       None if jac_cache is None else jac_cache.data_ptr(), int(alt_tableau))
+
+    def jac_cache(self, n_cells: int, device="cuda"):
+        """An empty (zeroed) W-method factorisation cache for n_cells cells (float64 tensor)."""
+        import torch
+        nbytes = int(self._lib.chem_jac_cache_bytes(self._h, n_cells))
+        return torch.zeros(nbytes // 8, dtype=torch.float64, device=device)
 
     def cost_order(self, cost, order=None, workspace=None, stream=None):
         """Cells by decreasing cost (int32 [C] device) -> order int32 [C] (chem_cost_order)."""

@@ -265,7 +265,8 @@ int read_spec(const char* path, MechData* m) {
 //   0 ROS4   Hairer & Wanner, Solving ODEs II, Sec. IV.7 (L-stable, order 4(3)) -- the default;
 //   1 ROS3   Sandu et al. (1997), order 3(2), L-stable;
 //   2 RODAS3 Sandu et al. (1997), order 3(2), stiffly accurate;
-//   3 RODAS4 Hairer & Wanner, Sec. VI.4, order 4(3), stiffly accurate.
+//   3 RODAS4 Hairer & Wanner, Sec. VI.4, order 4(3), stiffly accurate;
+//   5 ROS2   Verwer et al. (1999), a W-method of order 2(1), used with Jacobian reuse.
 struct RosCoefficients {
   int s = 0, order = 0;
   double gamma = 0;
@@ -275,6 +276,18 @@ struct RosCoefficients {
 
 RosCoefficients ros_coefficients(int id) {
   RosCoefficients t;
+  if (id == 5) {
+    // ROS2 (Verwer, Spee, Blom & Hundsdorfer 1999): second order for any matrix in place of the
+    // Jacobian (a W-method), L-stable with g = 1 + 1/sqrt(2); transformed: a21 = 1/g,
+    // c21 = -2/g, m = (3/(2g), 1/(2g)), error weights (1/(2g), 1/(2g))
+    t.s = 2; t.order = 2; t.gamma = 1.0 + 1.0 / std::sqrt(2.0);
+    const double g = t.gamma;
+    t.a[1][0] = 1.0 / g;
+    t.c[1][0] = -2.0 / g;
+    t.m[0] = 1.5 / g; t.m[1] = 0.5 / g;
+    t.e[0] = 0.5 / g; t.e[1] = 0.5 / g;
+    return t;
+  }
   if (id == 4) {
     // Runge-Kutta-Fehlberg 4(5): the fifth-order weights are propagated, their difference to the
     // fourth-order ones is the error estimate (controller exponent 1/5)
@@ -657,7 +670,7 @@ struct Module {
   CUmodule mod = nullptr;
   CUfunction f_source = nullptr, f_jac = nullptr, f_int = nullptr, f_pinit = nullptr, f_patt = nullptr,
              f_pfin = nullptr, f_adj = nullptr, f_adjred = nullptr, f_vjp = nullptr, f_ohist = nullptr,
-             f_oscan = nullptr, f_oscat = nullptr;
+             f_oscan = nullptr, f_oscat = nullptr, f_route = nullptr, f_rfall = nullptr;
   int smem = 0;          // dynamic shared memory per block
   int adj_smem = 0;      // ... of the adjoint / VJP kernels (0: not available for this config)
   int adj_occ = 0;
@@ -730,7 +743,7 @@ int smem_bytes(const MechData& m, int team, int tpb, int tableau) {
 int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = false, int tableau = 0,
                const std::string* prebuilt = nullptr) {
   std::lock_guard<std::mutex> lk(m->mu);
-  if (tableau < 0 || tableau > 4) return fail(CHEM_EARG, "unknown integration method %d", tableau);
+  if (tableau < 0 || tableau > 5) return fail(CHEM_EARG, "unknown integration method %d", tableau);
   auto key = std::make_tuple(team, tpb, tableau);
   auto& mods = adjoint ? m->adj_modules : m->modules;
   auto it = mods.find(key);
@@ -761,6 +774,8 @@ int get_module(chem_mech* m, int team, int tpb, Module** out, bool adjoint = fal
   CU_TRY(drv::cuModuleGetFunction(&mod->f_ohist, mod->mod, "chem_order_hist_k"));
   CU_TRY(drv::cuModuleGetFunction(&mod->f_oscan, mod->mod, "chem_order_scan_k"));
   CU_TRY(drv::cuModuleGetFunction(&mod->f_oscat, mod->mod, "chem_order_scatter_k"));
+  CU_TRY(drv::cuModuleGetFunction(&mod->f_route, mod->mod, "chem_route_k"));
+  CU_TRY(drv::cuModuleGetFunction(&mod->f_rfall, mod->mod, "chem_route_fallback_k"));
   CUdeviceptr slots_ptr;
   size_t slots_sz;
   CU_TRY(drv::cuModuleGetGlobal(&slots_ptr, &slots_sz, mod->mod, "chem_slots"));
@@ -878,7 +893,7 @@ int chem_mech_compile_only(const char* spec_path, const chem_build_opts* opts, c
   const bool adj = opts && opts->adjoint;
   if (adj && team < 32) return fail(CHEM_EARG, "the adjoint needs a multi-lane configuration (team >= 32)");
   const int tab = opts ? opts->tableau : 0;
-  if (tab < 0 || tab > 4) return fail(CHEM_EARG, "unknown integration method %d", tab);
+  if (tab < 0 || tab > 5) return fail(CHEM_EARG, "unknown integration method %d", tab);
   if (adj && tab != 0) return fail(CHEM_EARG, "the adjoint is implemented for ROS4 (tableau 0)");
   int rc = build_cubin(d, team, tpb, adj, tab, opts ? opts->cache_dir : nullptr, opts && opts->verbose, &cubin, &lg);
   if (log && log_cap) {
@@ -978,6 +993,8 @@ size_t chem_integrate_workspace(chem_mech_t m, int64_t n_cells, const chem_int_o
     const int max_steps = (o && o->max_steps > 0) ? o->max_steps : 100000;
     return plain_layout((int)m->data.sp.size(), n_cells, max_steps).total;
   }
+  if (o && o->cell_method)  // two queue counters, list lengths, two cell lists, explicit status
+    return 512 + 3 * align256(sizeof(int) * (size_t)n_cells);
   return 256;
 }
 
@@ -1017,6 +1034,61 @@ int chem_integrate(chem_mech_t m, int64_t n_cells, double* T, const double* P, d
   if (int rc = resolve(m, o, &mod)) return rc;
   long long nc = n_cells, l = ld;
   CUstream s = (CUstream)stream;
+  double* wjc = o ? o->jac_cache : nullptr;  // W-method factorisation cache
+  const int alt = (o && o->alt_tableau) ? o->alt_tableau : 4;
+  if (wjc && !(o->tableau == 5 || (o->cell_method && alt == 5)))
+    return fail(CHEM_EARG, "jac_cache needs the W-method (tableau 5, or alt_tableau 5 with cell_method)");
+  if (wjc && mode != CHEM_MODE_PERSISTENT) return fail(CHEM_EARG, "jac_cache needs the persistent driver");
+  if (wjc && (((uintptr_t)wjc) & 7)) return fail(CHEM_EARG, "jac_cache must be 8-byte aligned");
+  if (mode == CHEM_MODE_PERSISTENT && o && o->cell_method) {
+    // per-cell method switching: route, explicit launch, fall back, implicit launch
+    if (o->tableau < 0 || o->tableau > 3)
+      return fail(CHEM_EARG, "per-cell method switching needs a Rosenbrock method (tableau 0..3)");
+    if (alt != 4 && alt != 5) return fail(CHEM_EARG, "alt_tableau must be CHEM_RKF45 or CHEM_ROS2W");
+    if (alt == 5 && !wjc) return fail(CHEM_EARG, "switching to the W-method needs jac_cache");
+    Module* emod;
+    if (int rc = get_module(m, mod->team, mod->tpb, &emod, false, alt)) return rc;
+    char* b = (char*)ws;
+    const CUdeviceptr qe = (CUdeviceptr)b, qi = (CUdeviceptr)(b + 64);
+    unsigned* counts = (unsigned*)(b + 256);
+    const size_t li = align256(sizeof(int) * (size_t)n_cells);
+    int* list_e = (int*)(b + 512);
+    int* list_i = (int*)(b + 512 + li);
+    int* st_e = (int*)(b + 512 + 2 * li);
+    int* cm = o->cell_method;
+    CU_TRY(drv::cuMemsetD32Async((CUdeviceptr)counts, 0, 2, s));
+    CU_TRY(drv::cuMemsetD32Async(qe, 0, 2, s));
+    CU_TRY(drv::cuMemsetD32Async(qi, 0, 2, s));
+    const unsigned g256 = (unsigned)((n_cells + 255) / 256);
+    {
+      void* a[] = {&nc, &cm, &list_e, &list_i, &counts};
+      CU_TRY(drv::cuLaunchKernel(mod->f_route, g256, 1, 1, 256, 1, 1, 0, s, a, nullptr));
+    }
+    int* tnacc = nullptr;
+    double* th = nullptr;
+    double* tck = nullptr;
+    int cap = 0, interval = 1;
+    {
+      CUdeviceptr q = qe;
+      const unsigned* cnt = counts;
+      int keep = 1, am = 1;
+      void* a[] = {&nc, &T, (void*)&P, &Y, &l, &dt, &rtol, &atol, &h, &st_e, &att, (void*)&lnA,
+                   &max_steps, &h_min, &T_min, &q, &tnacc, &th, &tck, &cap, &interval, &list_e,
+                   (void*)&cnt, &keep, &cm, &am, &wjc};
+      if (int rc = launch(emod->f_int, grid_for(m, emod, n_cells), emod, stream, a)) return rc;
+    }
+    {
+      void* a[] = {&nc, &list_e, &counts, &st_e, &list_i, &status};
+      CU_TRY(drv::cuLaunchKernel(mod->f_rfall, g256, 1, 1, 256, 1, 1, 0, s, a, nullptr));
+    }
+    CUdeviceptr q = qi;
+    const unsigned* cnt = counts + 1;
+    int keep = 0, am = alt == 5 ? 3 : 2;
+    void* a[] = {&nc, &T, (void*)&P, &Y, &l, &dt, &rtol, &atol, &h, &status, &att, (void*)&lnA,
+                 &max_steps, &h_min, &T_min, &q, &tnacc, &th, &tck, &cap, &interval, &list_i,
+                 (void*)&cnt, &keep, &cm, &am, &wjc};
+    return launch(mod->f_int, grid_for(m, mod, n_cells), mod, stream, a);
+  }
   if (mode == CHEM_MODE_PERSISTENT) {
     CUdeviceptr q = (CUdeviceptr)ws;
     CU_TRY(drv::cuMemsetD32Async(q, 0, 2, s));
@@ -1026,9 +1098,11 @@ int chem_integrate(chem_mech_t m, int64_t n_cells, double* T, const double* P, d
     int cap = 0, interval = 1, keep = 0;
     const int32_t* order = o ? o->order : nullptr;
     const unsigned* ocount = nullptr;
+    int* cm = nullptr;
+    int am = 0;
     void* args[] = {&nc, &T, (void*)&P, &Y, &l, &dt, &rtol, &atol, &h, &status, &att, (void*)&lnA,
                     &max_steps, &h_min, &T_min, &q, &tnacc, &th, &tck, &cap, &interval,
-                    (void*)&order, (void*)&ocount, &keep};
+                    (void*)&order, (void*)&ocount, &keep, &cm, &am, &wjc};
     return launch(mod->f_int, grid_for(m, mod, n_cells), mod, stream, args);
   }
   if (mode != CHEM_MODE_PLAIN) return fail(CHEM_EARG, "unknown mode %d", mode);
@@ -1080,6 +1154,9 @@ int chem_integrate_host(chem_mech_t m, int64_t n_cells, double* T, const double*
   chem_int_opts oo = o ? *o : chem_int_opts{};
   oo.mode = CHEM_MODE_PERSISTENT;
   oo.attempts = nullptr;
+  oo.order = nullptr;
+  oo.cell_method = nullptr;
+  oo.jac_cache = nullptr;
   const size_t n = (size_t)n_cells;
   const size_t offT = 0, offP = align256(offT + 8 * n), offY = align256(offP + 8 * n),
                offH = align256(offY + 8 * n * ns), offS = align256(offH + 8 * n), offW = align256(offS + 4 * n);
@@ -1174,9 +1251,13 @@ int chem_integrate_ckpt(chem_mech_t m, int64_t n_cells, double* T, const double*
   const int32_t* order = o ? o->order : nullptr;
   const unsigned* ocount = nullptr;
   int keep = 0;
+  int* cm = nullptr;
+  int am = 0;
+  if (o && o->cell_method) return fail(CHEM_EARG, "the checkpointed forward has no per-cell method switching");
+  double* wjc = nullptr;
   void* args[] = {&nc, &T, (void*)&P, &Y, &l, &dt, &rtol, &atol, &h, &status, &att, (void*)&lnA,
                   &max_steps, &h_min, &T_min, &q, &tnacc, &th, &tck, &cap, &interval, (void*)&order,
-                  (void*)&ocount, &keep};
+                  (void*)&ocount, &keep, &cm, &am, &wjc};
   return launch(mod->f_int, grid_for(m, mod, n_cells), mod, stream, args);
 }
 
@@ -1331,6 +1412,13 @@ int chem_eval_vjp(chem_mech_t m, int64_t n_cells, const double* T, const double*
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_cells + tpb - 1) / tpb, (int64_t)m->n_sm * mod->adj_occ));
   CU_TRY(drv::cuLaunchKernel(mod->f_vjp, grid, 1, 1, mod->tpb, 1, 1, mod->adj_smem, (CUstream)stream, args, nullptr));
   return 0;
+}
+
+size_t chem_jac_cache_bytes(chem_mech_t m, int64_t n_cells) {
+  if (!m || n_cells < 0) return 0;
+  const size_t ns = m->data.sp.size();
+  const size_t stride = ns * ns + 2 * ((ns + 1) / 2) + 2;  // WC_STRIDE of ros4_device.cuh
+  return sizeof(double) * stride * (size_t)n_cells;
 }
 
 size_t chem_cost_order_workspace(void) { return 256 + 2 * 1024 * sizeof(unsigned); }

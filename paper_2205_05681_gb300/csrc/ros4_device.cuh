@@ -122,6 +122,19 @@
 #endif
 #define UOFF(i) ((i) == 0 ? OFF_U1 : OFF_U2 + ((i) - 1) * NEQ)
 
+// Per-cell cache of the W-method's factorised iteration matrix (chem_int_opts.jac_cache, global
+// memory, one contiguous block per cell whatever the launch configuration): the N x N factors with
+// 1/U_kk on the diagonal, the composed row permutation and the pivot sequence (packed ints), the
+// step size h_W they were built for (0: empty) and their age in accepted steps.  A new factorisation
+// (Jacobian at the attempt's state) is made when h_W differs from the attempt's step size or
+// the age reaches WAGE_MAX.
+#define WC_PERM (NEQ * NEQ)
+#define WC_PIV (WC_PERM + PACKED_INTS(NEQ))
+#define WC_H (WC_PIV + PACKED_INTS(NEQ))
+#define WC_AGE (WC_H + 1)
+#define WC_STRIDE (WC_AGE + 1)
+#define WAGE_MAX 32
+
 // ------------------------------------------------------------------------------ team plumbing
 
 // mask of the calling lane's team within its warp (all lanes for TEAM >= 32)
@@ -175,6 +188,27 @@ __device__ __forceinline__ double team_sum(const Team& tm, double v) {
   __syncthreads();
   v = 0.0;
   for (int w = 0; w < TEAM / 32; ++w) v += red[w];
+  __syncthreads();
+#endif
+  return v;
+#endif
+}
+
+// maximum over the team (same reduction tree as team_sum)
+__device__ __forceinline__ double team_max(const Team& tm, double v) {
+#if TEAM == 1
+  return v;
+#else
+  const unsigned msk = team_mask();
+#pragma unroll
+  for (int o = XOR0; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(msk, v, o));
+#if TEAM > 32
+  double* red = &tm.base[OFF_RED];
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = red[0];
+  for (int w = 1; w < TEAM / 32; ++w) v = fmax(v, red[w]);
   __syncthreads();
 #endif
   return v;
@@ -831,7 +865,7 @@ __device__ __forceinline__ void stage_solve(const Team& tm, int ob) {
 
 template <bool REG_SOLVE = (NB >= 3)>
 __device__ double ros4_attempt(const Team& tm, double P, double hh, double rtol, double atol,
-                              const double* lnA_ext) {
+                              const double* lnA_ext, double* rho = nullptr, double* wc = nullptr) {
 #if ERK
   // explicit Runge-Kutta (RKF45) in increment form: u_i = hh f(y + sum_{j<i} a_ij u_j); no
   // Jacobian, no factorisation
@@ -852,13 +886,56 @@ __device__ double ros4_attempt(const Team& tm, double P, double hh, double rtol,
     tsync();
   }
 #else
-  // stage 1: f0 into U1, M = I/(gamma h) - J
-  eval_f_jac(tm, OFF_Y, OFF_U1, P, lnA_ext, -1.0, 1.0 / (RGAM * hh));
+  // stage 1: f0 into U1, M = I/(gamma h) - J (with a W-method cache: the cached factorisation
+  // of I/(gamma h) - W when it was made for this step size and is young enough)
+  const bool reuse = wc && wc[WC_H] == hh && wc[WC_AGE] < WAGE_MAX;
+  if (reuse) {
+    eval_f(tm, OFF_Y, OFF_U1, P, lnA_ext);
+    for (int e = tm.tl; e < NEQ * NEQ; e += TEAM) tm.at(OFF_A, e) = wc[e];
+    for (int e = tm.tl; e < PACKED_INTS(NEQ); e += TEAM) {
+      tm.at(OFF_PERM, e) = wc[WC_PERM + e];
+#if TEAM == 1
+      tm.at(OFF_PIV, e) = wc[WC_PIV + e];
+#endif
+    }
+    tsync();
+  } else {
+    eval_f_jac(tm, OFF_Y, OFF_U1, P, lnA_ext, -1.0, 1.0 / (RGAM * hh));
+  }
+  if (rho && !reuse) {
+    // stiffness estimate: Gershgorin bound of the Jacobian scaled by the error weights,
+    // max_i sum_j |J_ij| w_j / w_i with w = atol + rtol |y| (J_ij = -A_ij off the diagonal,
+    // shift - A_ii on it)
+    const double shift = 1.0 / (RGAM * hh);
+    double mx = 0.0;
+    for (int i = tm.tl; i < NEQ; i += TEAM) {
+      double sum = 0.0;
+      for (int j = 0; j < NEQ; ++j) {
+        const double a = tm.A(i, j);
+        sum += fabs(i == j ? shift - a : a) * (atol + rtol * fabs(tm.at(OFF_Y, j)));
+      }
+      const double r = sum / (atol + rtol * fabs(tm.at(OFF_Y, i)));
+      mx = r > mx ? r : mx;
+    }
+    *rho = team_max(tm, mx);
+  }
 #if NEED_F0
   for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(OFF_F0, i) = tm.at(OFF_U1, i);
   tsync();
 #endif
-  lu_factor(tm);
+  if (!reuse) {
+    lu_factor(tm);
+    if (wc) {  // keep the factorisation for later attempts of this size
+      for (int e = tm.tl; e < NEQ * NEQ; e += TEAM) wc[e] = tm.at(OFF_A, e);
+      for (int e = tm.tl; e < PACKED_INTS(NEQ); e += TEAM) {
+        wc[WC_PERM + e] = tm.at(OFF_PERM, e);
+#if TEAM == 1
+        wc[WC_PIV + e] = tm.at(OFF_PIV, e);
+#endif
+      }
+      if (tm.tl == 0) { wc[WC_H] = hh; wc[WC_AGE] = 0.0; }
+    }
+  }
   stage_solve<REG_SOLVE>(tm, OFF_U1);
   const double ih = 1.0 / hh;
 #pragma unroll
@@ -922,6 +999,9 @@ struct Ctl {
   bool reject_last, done;
   bool acc;   // the last call accepted a step ...
   double hh;  // ... of this size
+  bool want_rho;  // estimate the stiffness at the cell's first attempt (into rho)
+  double rho;
+  double* wc;     // the cell's W-method cache (global memory) or nullptr
 };
 
 // One attempt plus the controller decision (identical rules to the CPU oracle):
@@ -937,7 +1017,8 @@ __device__ __forceinline__ void ros4_advance(const Team& tm, Ctl& c, double P, d
   if (c.h < h_min) { c.status = ST_H_UNDERFLOW; c.done = true; return; }
   const bool last = c.t + 1.0001 * c.h >= dt;
   const double hh = last ? dt - c.t : c.h;
-  const double err = ros4_attempt(tm, P, hh, rtol, atol, lnA_ext);
+  const double err = ros4_attempt(tm, P, hh, rtol, atol, lnA_ext,
+                                  (c.want_rho && c.attempts == 0) ? &c.rho : nullptr, c.wc);
   c.attempts++;
   const bool finite = isfinite(err);
   double fac = 0.2;
@@ -954,6 +1035,7 @@ __device__ __forceinline__ void ros4_advance(const Team& tm, Ctl& c, double P, d
   }
   if (finite && err <= 1.0) {
     for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(OFF_Y, i) = tm.at(OFF_YT, i);
+    if (c.wc && tm.tl == 0) c.wc[WC_AGE] += 1.0;  // the cached factorisation ages per accepted step
     tsync();
     if (c.reject_last && fac > 1.0) fac = 1.0;
     c.reject_last = false;
@@ -1079,6 +1161,23 @@ chem_eval_jacobian_k(long long n_cells, const double* __restrict__ T, const doub
   }
 }
 
+// Per-cell method switching (chem_int_opts.cell_method): a launch of the alternative method's
+// module (RKF45, or the W-method with its factorisation cache) runs the cells marked for it under
+// their attempt budgets and keeps the input of any that fails; a launch of the Rosenbrock module
+// runs the others and the failed ones and marks each cell for the next call:
+//   * alternative RKF45 (AUTO_IMPLICIT): when dt * rho <= STIFF_BETA * attempts, rho the stiffness
+//     estimate at the cell's first attempt (the explicit method's stability-limited steps, about
+//     dt * rho / STIFF_BETA, would not outnumber the Rosenbrock attempts);
+//   * alternative W-method (AUTO_IMPLICIT_W): when the cell took a single attempt (a quiescent
+//     cell, whose split steps the cached factorisation can serve); its cache is emptied, so the
+//     W-method starts from a Jacobian at its own state;
+// with budget 4 * attempts + 8; after a success of the alternative method with a attempts, it
+// stays with budget 4a + 8.
+#define AUTO_EXPLICIT 1
+#define AUTO_IMPLICIT 2
+#define AUTO_IMPLICIT_W 3
+#define STIFF_BETA 3.0
+
 // Persistent driver: each team pulls cells from the queue counter and integrates them to dt.
 // With TEAM == 1 each thread refills independently (per-lane refill of retired cells); the
 // loop body is one step attempt so that lanes on different cells still execute it together.
@@ -1095,7 +1194,8 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
                  int max_steps, double h_min, double T_min, unsigned long long* queue,
                  int* __restrict__ tape_nacc, double* __restrict__ tape_h, double* __restrict__ tape_ck,
                  int tape_cap, int interval, const int* __restrict__ order,
-                 const unsigned int* __restrict__ order_count, int keep_failed) {
+                 const unsigned int* __restrict__ order_count, int keep_failed,
+                 int* __restrict__ cell_method, int auto_mode, double* __restrict__ jac_cache) {
   extern __shared__ double smem[];
   const Team tm = make_team(smem);
   long long cell = -1;
@@ -1103,7 +1203,11 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
   Ctl c;
   c.done = true;
   c.acc = false;
+  c.want_rho = false;
+  c.rho = 0.0;
+  c.wc = nullptr;
   int nacc = 0;
+  int ms_cell = max_steps;
   // queue positions: n_cells, or the device-held length of the cell list `order`
   const long long nq = order_count ? (long long)*order_count : n_cells;
   // bounded: every iteration either retires a cell or makes an attempt (<= max_steps per cell),
@@ -1128,6 +1232,16 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
       c.status = ST_OK;
       c.reject_last = false;
       c.done = false;
+      c.want_rho = auto_mode == AUTO_IMPLICIT;
+      c.rho = 0.0;
+      // the W-method's factorisation cache (not used by a Rosenbrock launch of the switching)
+      c.wc = (jac_cache && auto_mode != AUTO_IMPLICIT_W) ? jac_cache + cell * (long long)WC_STRIDE : nullptr;
+      // per-cell method switching: an explicit cell runs under its attempt budget
+      ms_cell = max_steps;
+      if (auto_mode == AUTO_EXPLICIT) {
+        const int b = cell_method[cell];
+        ms_cell = b > 0 && b < max_steps ? b : max_steps;
+      }
       const bool ok = load_cell(tm, cell, T, Y, ld);
       nacc = 0;
       if (!ok || tm.at(OFF_Y, 0) < T_min) {
@@ -1149,7 +1263,7 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
       c.status = ST_TAPE_FULL;
       c.done = true;
     } else {
-      ros4_advance(tm, c, Pc, dt, rtol, atol, max_steps, h_min, lnA_ext);
+      ros4_advance(tm, c, Pc, dt, rtol, atol, ms_cell, h_min, lnA_ext);
     }
     if (tape_h && c.acc && c.status != ST_TAPE_FULL) {
       // record the accepted step; checkpoint the state after every `interval` accepted steps
@@ -1161,13 +1275,23 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
     }
     if (c.done) {
       if (tm.tl == 0 && tape_nacc) tape_nacc[cell] = nacc;
-      // keep_failed: a cell that did not reach dt leaves its input state in place (a later launch
-      // integrates it again from the start)
-      if (!(keep_failed && c.status != ST_OK)) store_cell(tm, cell, T, Y, ld);
+      // keep_failed: a cell that did not reach dt leaves its input state and step size in place
+      // (a later launch integrates it again from the start)
+      const bool keep = keep_failed && c.status != ST_OK;
+      if (!keep) store_cell(tm, cell, T, Y, ld);
       if (tm.tl == 0) {
-        if (h_io) h_io[cell] = c.h;
+        if (h_io && !keep) h_io[cell] = c.h;
         if (status_out) status_out[cell] = c.status;
         if (attempts_out) attempts_out[cell] = c.attempts;
+        if (auto_mode == AUTO_EXPLICIT)  // success: stay explicit, budget from this run
+          cell_method[cell] = c.status == ST_OK ? 4 * c.attempts + 8 : 0;
+        else if (auto_mode == AUTO_IMPLICIT)  // explicit next time if its stable steps are few
+          cell_method[cell] = (c.status == ST_OK && dt * c.rho <= STIFF_BETA * c.attempts)
+                                  ? 4 * c.attempts + 8 : 0;
+        else if (auto_mode == AUTO_IMPLICIT_W) {  // the W-method next time if quiescent
+          cell_method[cell] = (c.status == ST_OK && c.attempts == 1) ? 12 : 0;
+          if (jac_cache) jac_cache[cell * (long long)WC_STRIDE + WC_H] = 0.0;
+        }
       }
       tsync();
     }
@@ -1211,6 +1335,31 @@ extern "C" __global__ void chem_order_scatter_k(long long n_cells, const int* __
   const int v = cost[c];
   const unsigned int pos = atomicAdd(&starts[v < 0 ? 0 : (v >= ORDER_BINS ? ORDER_BINS - 1 : v)], 1u);
   order[pos] = (int)c;
+}
+
+// Per-cell method switching: split the cells into the explicit list (cell_method > 0) and the
+// implicit list; counts[0], counts[1] their lengths (zeroed by the caller).
+extern "C" __global__ void chem_route_k(long long n_cells, const int* __restrict__ cell_method,
+                                        int* __restrict__ list_e, int* __restrict__ list_i,
+                                        unsigned int* __restrict__ counts) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  if (cell_method[c] > 0) list_e[atomicAdd(&counts[0], 1u)] = (int)c;
+  else list_i[atomicAdd(&counts[1], 1u)] = (int)c;
+}
+
+// After the explicit launch: its cells that ran out of budget (or step size) go to the end of the
+// implicit list; the others' status is final and is copied to the caller's array.
+extern "C" __global__ void chem_route_fallback_k(long long n_cells, const int* __restrict__ list_e,
+                                                 unsigned int* __restrict__ counts, const int* __restrict__ st_e,
+                                                 int* __restrict__ list_i, int* __restrict__ status_out) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)counts[0]) return;
+  const int c = list_e[q];
+  if (c < 0 || c >= n_cells) return;
+  const int s = st_e[c];
+  if (s == ST_MAX_STEPS || s == ST_H_UNDERFLOW) list_i[atomicAdd(&counts[1], 1u)] = c;
+  else if (status_out) status_out[c] = s;
 }
 
 // Plain driver, one launch per step attempt over all cells.  Per-cell controller state lives
@@ -1274,6 +1423,8 @@ chem_plain_attempt_k(long long n_cells, double* __restrict__ T, const double* __
     c.status = ST_OK;
     c.reject_last = (fl & 2) != 0;
     c.done = false;
+    c.want_rho = false;
+    c.wc = nullptr;
     ros4_advance(tm, c, P[cell], dt, rtol, atol, max_steps, h_min, lnA_ext);
     if (c.done) {
       store_cell(tm, cell, T, Y, ld);

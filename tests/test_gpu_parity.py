@@ -608,3 +608,108 @@ def test_cost_ordered_queue(omech, mech_path):
     # cost buckets above 1023 share the top bucket; negative costs the bottom one
     cost = torch.tensor(np.array([5, 2000, -3, 1023, 7], dtype=np.int32), device=T0.device)
     assert g.cost_order(cost).cpu().numpy().tolist()[2:] == [4, 0, 2]
+
+
+@pytest.mark.parametrize("name,team,block,alt", [("h2_13", 4, 64, 4), ("h2_13", 64, 64, 4),
+                                                 ("ch4_53", 64, 64, 4), ("h2_13", 4, 64, 5),
+                                                 ("ch4_111", 256, 256, 5)])
+def test_per_cell_method_switching(omech, gmech, name, team, block, alt):
+    """Per-cell switching between an alternative method (RKF45 by the stiffness rule, or the
+    W-method with its factorisation cache for quiescent cells) and ROS4 over consecutive split
+    steps (the method array carried like h) against the oracle running the same policy: the same
+    method choices, and per cell the oracle's state within 1e-5 when its attempt counts match
+    (flip rule as elsewhere)."""
+    import torch
+    om = omech(name)
+    g = gmech(name, team, block)
+    n = {"h2_13": 600, "ch4_53": 120, "ch4_111": 40}[name]
+    nsplit, dt = (3 if alt == 4 else 5), 1e-6
+    if name == "ch4_111":  # relaxed product cells and ignition-front cells
+        st, _ = _front_inputs(om, n, 17)
+        y0 = om.state_from_TY(st.T, st.Y)
+    else:
+        st, y0 = _inputs(om, name, n, 151)
+    T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    h = torch.zeros(n, dtype=torch.float64, device=T.device)
+    att = torch.zeros(n, dtype=torch.int32, device=T.device)
+    status = torch.full((n,), -1, dtype=torch.int32, device=T.device)
+    meth = torch.zeros(n, dtype=torch.int32, device=T.device)
+    jc = g.jac_cache(n) if alt == 5 else None
+    o = g.opts(attempts=att, cell_method=meth, jac_cache=jc, alt_tableau=alt)
+    ws = g.workspace(n, o)
+    cache = om.w_cache(n) if alt == 5 else None
+    y, hh = y0.copy(), np.zeros(n)
+    mo = np.zeros(n, dtype=np.int32)
+    same = np.ones(n, dtype=bool)
+    for s in range(nsplit):
+        g.integrate(T, P, Y, dt, h=h, status=status, opts=o, workspace=ws)
+        y, info = om.integrate_auto(y, st.P, dt, mo, h=hh, threads=16, alt=alt, cache=cache)
+        hh = info["h"]
+        assert (status.cpu().numpy() == 0).all() and np.all(info["status"] == 0)
+        mg = meth.cpu().numpy()
+        same &= (mg == mo) & (att.cpu().numpy() == info["attempts"])
+        assert (mg != mo).mean() <= 0.02, (s, (mg != mo).sum())
+    if alt == 5:
+        assert (mo > 0).mean() > 0.3  # quiescent cells move to the W-method
+    elif name == "h2_13":
+        assert (mo > 0).mean() > 0.5  # most of these cells run explicitly after the first step
+    else:
+        assert (mo == 0).all()  # stiff cells stay on the Rosenbrock method
+    yg = gpu_state(om, T, Y)
+    e = weighted_norm(y, yg)
+    assert np.all(e[same] <= 1e-5), (e[same].max(), np.argmax(np.where(same, e, 0)))
+    flips = np.where(~same)[0]
+    assert len(flips) <= max(1, int(0.02 * n)), len(flips)
+    if len(flips):
+        yt, _ = _oracle_splits(om, y0[flips], st.P[flips], dt, nsplit, rtol=1e-10, atol=1e-14)
+        assert np.all(weighted_norm(yt, yg[flips]) <= 10.0)
+
+
+@pytest.mark.parametrize("name,team,block", [("h2_13", 4, 64), ("ch4_53", 64, 64),
+                                             ("ch4_111", 256, 256)])
+def test_w_method_with_factorisation_reuse(omech, gmech, name, team, block):
+    """The W-method ROS2 with its factorisation cache carried over consecutive split steps against
+    the oracle's W-method with its Jacobian cache: the same reuse decisions (each cell's cache
+    step size and age after every split step) and states within 1e-5 for matching attempt
+    sequences (flip rule as elsewhere)."""
+    import torch
+    from paper_2205_05681_gb300 import chem
+    om = omech(name)
+    g = gmech(name, team, block)
+    n = {"h2_13": 400, "ch4_53": 96, "ch4_111": 24}[name]
+    nsplit, dt = 4, 1e-6
+    st, y0 = _inputs(om, name, n, 161)
+    if name == "ch4_111":  # relaxed product cells: the regime where the factorisation is reused
+        yq, _ = om.integrate(y0, st.P, 1e-4, threads=16)
+        st.T, st.Y = om.TY_from_state(yq)
+        y0 = om.state_from_TY(st.T, st.Y)
+    T, P, Y = to_dev(st.T), to_dev(st.P), to_dev(st.Y.T)
+    h = torch.zeros(n, dtype=torch.float64, device=T.device)
+    att = torch.zeros(n, dtype=torch.int32, device=T.device)
+    status = torch.full((n,), -1, dtype=torch.int32, device=T.device)
+    jc = g.jac_cache(n)
+    stride = jc.numel() // n
+    o = g.opts(attempts=att, tableau=chem.ROS2W, jac_cache=jc)
+    cache = om.w_cache(n)
+    y, hh = y0.copy(), np.zeros(n)
+    same = np.ones(n, dtype=bool)
+    reused = 0
+    for s in range(nsplit):
+        g.integrate(T, P, Y, dt, h=h, status=status, opts=o)
+        y, info = om.integrate_w(y, st.P, dt, cache, h=hh, threads=16)
+        hh = info["h"]
+        assert (status.cpu().numpy() == 0).all() and np.all(info["status"] == 0)
+        c = jc.view(n, stride).cpu().numpy()
+        same &= att.cpu().numpy() == info["attempts"]
+        same &= (c[:, -1] == cache[2]) & (np.abs(c[:, -2] - cache[1]) <= 1e-12 * cache[1])
+        if s > 0:
+            reused += int((info["n_jac"] == 0).sum())
+    assert reused > 0  # the cache was used across calls
+    yg = gpu_state(om, T, Y)
+    e = weighted_norm(y, yg)
+    assert np.all(e[same] <= 1e-5), (e[same].max(), np.argmax(np.where(same, e, 0)))
+    flips = np.where(~same)[0]
+    assert len(flips) <= max(1, int(0.02 * n)), len(flips)
+    if len(flips):
+        yt, _ = _oracle_splits(om, y0[flips], st.P[flips], dt, nsplit, rtol=1e-10, atol=1e-14)
+        assert np.all(weighted_norm(yt, yg[flips]) <= 10.0)

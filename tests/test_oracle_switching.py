@@ -4,6 +4,7 @@ the initial state when the explicit budget runs out, and the stiffness rule comp
 independently from the oracle's Jacobian."""
 import numpy as np
 
+from oracle import oracle as O
 from tests.conftest import states
 
 
@@ -69,3 +70,30 @@ def test_skipped_and_nonfinite_cells_keep_their_method(omech):
     y, info = om.integrate_auto(y0, st.P, 1e-6, meth, T_min=300.0)
     assert info["status"].tolist() == [0, 3, 4]
     assert meth[1] == 7 and meth[2] == 9
+
+
+def test_w_method_alternative_for_quiescent_cells(omech):
+    """With the W-method as the alternative: a cell whose Rosenbrock split step was one attempt
+    moves to the W-method (budget 12) and empties its cache; on the W-method it reuses the
+    factorisation across calls (cache age grows, step size kept)."""
+    om = omech("h2_13")
+    st = states("h2_13", 8, "h2_fresh", 405)
+    y0 = om.state_from_TY(st.T, st.Y)
+    yq, _ = om.integrate(y0[:4], st.P[:4], 1e-2)  # four relaxed cells, four fresh ones
+    y = np.concatenate([yq, y0[4:]])
+    meth = np.zeros(8, dtype=np.int32)
+    cache = om.w_cache(8)
+    h = np.zeros(8)
+    y1, i1 = om.integrate_auto(y, st.P, 1e-6, meth, h=h, alt=O.ROS2W, cache=cache)
+    assert np.all(cache[1] == 0.0)  # emptied by the Rosenbrock integration
+    yr, ir = om.integrate(y, st.P, 1e-6, threads=1)
+    assert np.array_equal(y1, yr)
+    assert np.array_equal(meth, np.where(ir["attempts"] == 1, 12, 0).astype(np.int32))
+    assert np.all(meth[:4] == 12)
+    y2, i2 = om.integrate_auto(y1, st.P, 1e-6, meth, h=i1["h"], alt=O.ROS2W, cache=cache)
+    assert np.all(i2["status"] == 0)
+    assert np.all(cache[1][:4] > 0) and np.all(cache[2][:4] == i2["attempts"][:4])
+    age = cache[2][:4].copy()
+    y3, i3 = om.integrate_auto(y2, st.P, 1e-6, meth, h=i2["h"], alt=O.ROS2W, cache=cache)
+    quiet = i3["attempts"][:4] == 1
+    assert quiet.any() and np.all(cache[2][:4][quiet] == age[quiet] + 1)  # reused, aged by one
