@@ -636,9 +636,15 @@ def forward_run(m, chem, torch, np, dev, T0, P, Y0, dt, splits, steps, warmup, r
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    # this library's kernels per bench step: the integrator per split step; with switching also
+    # the routing and fall-back kernels and the alternative method's integrator; with the cost
+    # order the three sorting kernels between split steps
+    per_split = 4 if switching else 1
+    launches = splits * per_split + (3 * (splits - 1) if (cost_order and splits > 1) else 0)
     res = {"times": times, "attempts": att_total.cpu().numpy(),
            "ok_cells": int((status == 0).sum().item()), "clocks": clk.summary(),
-           "explicit_cells": int((meth > 0).sum().item()) if switching else 0}
+           "explicit_cells": int((meth > 0).sum().item()) if switching else 0,
+           "launches_per_step": launches}
     if plain:
         # the plain one-launch-per-attempt driver on the same inputs (split steps run eagerly: its
         # host polling cannot be captured in a graph); one run, its kernels are already loaded
@@ -903,7 +909,7 @@ def main():
             "d2h_bytes_per_step": int(splits * (8 * n_cells * (1 + N + 1) + 4 * n_cells)),
             "host_memory": "pinned", "host_calls_per_step": splits},
         "cpu_baseline": cpu,
-        "gpu_launches": args.steps * splits,
+        "gpu_launches": args.steps * run["launches_per_step"],
         "clocks": clk,
         "mech_load_s": load_s,
     }

@@ -648,7 +648,8 @@ def test_per_cell_method_switching(omech, gmech, name, team, block, alt):
         assert (status.cpu().numpy() == 0).all() and np.all(info["status"] == 0)
         mg = meth.cpu().numpy()
         same &= (mg == mo) & (att.cpu().numpy() == info["attempts"])
-        assert (mg != mo).mean() <= 0.02, (s, (mg != mo).sum())
+        # the method chosen for the next split step (its budget follows the attempt count)
+        assert ((mg > 0) != (mo > 0)).mean() <= 0.02, (s, ((mg > 0) != (mo > 0)).sum())
     if alt == 5:
         assert (mo > 0).mean() > 0.3  # quiescent cells move to the W-method
     elif name == "h2_13":
@@ -659,7 +660,8 @@ def test_per_cell_method_switching(omech, gmech, name, team, block, alt):
     e = weighted_norm(y, yg)
     assert np.all(e[same] <= 1e-5), (e[same].max(), np.argmax(np.where(same, e, 0)))
     flips = np.where(~same)[0]
-    assert len(flips) <= max(1, int(0.02 * n)), len(flips)
+    # a flip can happen at every split step's decisions: at most 2% of the cells per split step
+    assert len(flips) <= max(1, int(0.02 * n * nsplit)), len(flips)
     if len(flips):
         yt, _ = _oracle_splits(om, y0[flips], st.P[flips], dt, nsplit, rtol=1e-10, atol=1e-14)
         assert np.all(weighted_norm(yt, yg[flips]) <= 10.0)
@@ -709,7 +711,8 @@ def test_w_method_with_factorisation_reuse(omech, gmech, name, team, block):
     e = weighted_norm(y, yg)
     assert np.all(e[same] <= 1e-5), (e[same].max(), np.argmax(np.where(same, e, 0)))
     flips = np.where(~same)[0]
-    assert len(flips) <= max(1, int(0.02 * n)), len(flips)
+    # a flip can happen at every split step's decisions: at most 2% of the cells per split step
+    assert len(flips) <= max(1, int(0.02 * n * nsplit)), len(flips)
     if len(flips):
         yt, _ = _oracle_splits(om, y0[flips], st.P[flips], dt, nsplit, rtol=1e-10, atol=1e-14)
         assert np.all(weighted_norm(yt, yg[flips]) <= 10.0)
