@@ -51,9 +51,8 @@ METHODS = ["ROS4", "ROS3", "RODAS3", "RODAS4", "RKF45", "ROS2W"]
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one chem_integrate_k launch on the
 # full bench workload, from a single-pass ncu capture; valid only for the device source they were
 # taken on (sha1 of csrc/ros4_device.cuh), reported as null once that source changes.
-MEASURED_TRAFFIC = {"device_src_sha1": "4eaa7cff46fc88307181e4fc58f1bbdbf0870669",
-                    "ch4_53_fwd": 30446592 + 1089536,
-                    "ch4_111_batched": 262365696 + 242472448}
+MEASURED_TRAFFIC = {"device_src_sha1": "3eb154b40f5040d20298a37237fce177a1110511",
+                    "ch4_111_batched": 253508864 + 207848192}
 
 
 def measured_traffic(wl, full_size):
