@@ -107,18 +107,21 @@ typedef struct {
                           the cells in this order -- a permutation of 0..n_cells-1, e.g. the
                           cost order of chem_cost_order; entries outside [0, n_cells) are skipped.
                           The results of a cell do not depend on the order. */
-  int32_t* cell_method; /* device [n_cells] in/out (nullable): per-cell switching between the
-                          explicit RKF45 and the Rosenbrock method `tableau` (persistent mode;
-                          workspace per chem_integrate_workspace).  In: > 0 = integrate the cell
-                          with RKF45 under at most that many attempts, falling back to the
-                          Rosenbrock method from the cell's initial state if it does not reach
-                          dt within them; <= 0 = the Rosenbrock method.  Out: the choice for the
-                          next call -- after RKF45 succeeded with a attempts, 4a + 8; after a
-                          Rosenbrock integration with a attempts, 4a + 8 if dt * rho <= 3a
-                          (rho = max_i sum_j |J_ij| w_j / w_i at the first attempt, w = atol +
-                          rtol |y|: the explicit method's stability-limited steps would not
-                          outnumber the Rosenbrock attempts), else 0.  Start from zeros.
-                          attempts/status report the run that finished the cell. */
+  int32_t* cell_method; /* device [n_cells] in/out (nullable): per-cell switching between an
+                          alternative method (alt_tableau: RKF45 by default) and the Rosenbrock
+                          method `tableau` (0..3; persistent mode; workspace per
+                          chem_integrate_workspace).  In: > 0 = integrate the cell with the
+                          alternative method under at most that many attempts, falling back to
+                          the Rosenbrock method from the cell's initial state and step size if it
+                          does not reach dt within them; <= 0 = the Rosenbrock method.  Out: the
+                          choice for the next call -- after the alternative succeeded with a
+                          attempts, 4a + 8; after a Rosenbrock integration with a attempts (RKF45
+                          alternative), 4a + 8 if dt * rho <= 3a (rho = max_i sum_j |J_ij| w_j / w_i
+                          at the first attempt, w = atol + rtol |y|: the explicit method's
+                          stability-limited steps would not outnumber the Rosenbrock attempts),
+                          else 0.  Start from zeros.  attempts/status report the run that finished
+                          the cell.  Launches, on `stream`: a routing kernel, the alternative
+                          method's integrator, a fall-back kernel, the Rosenbrock integrator. */
   double* jac_cache;    /* device, chem_jac_cache_bytes(n_cells) bytes, 8-byte aligned (nullable;
                           only with CHEM_ROS2W, persistent mode): per cell the factorised matrix
                           I/(gamma h) - W of the W-method, the step size it was built for and its

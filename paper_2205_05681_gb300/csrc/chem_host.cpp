@@ -709,7 +709,8 @@ int slots_for(const MechData& m, int tableau, int team) {
   const int ns = (int)m.sp.size();
   const RosCoefficients c = ros_coefficients(tableau);
   const int packed = (ns + 1) / 2;
-  return ns * ns + (8 + c.s + (needs_f0(c) ? 1 : 0)) * ns + packed * (team == 1 ? 2 : 1) + 24;
+  // stage slots: at least three after the stage argument (the Jacobian assembly aliases them)
+  return ns * ns + (8 + std::max(c.s, 3) + (needs_f0(c) ? 1 : 0)) * ns + packed * (team == 1 ? 2 : 1) + 24;
 }
 
 // distance in doubles between consecutive teams' slots (TSTRIDE of ros4_device.cuh): sub-warp

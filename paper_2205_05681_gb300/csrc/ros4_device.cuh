@@ -88,11 +88,14 @@
 #define OFF_U2 (OFF_YT + NEQ)
 #define OFF_U3 (OFF_U2 + NEQ)
 #define OFF_U4 (OFF_U3 + NEQ)
+// at least three stage slots after the stage argument (YT, U2, U3): the Jacobian assembly's
+// three per-species arrays alias them (a two-stage method has no U3 of its own)
+#define NSTG (RS > 3 ? RS : 3)
 #if NEED_F0
-#define OFF_F0 (OFF_U2 + (RS - 1) * NEQ)  // f(y) kept for a later stage whose argument is y itself
+#define OFF_F0 (OFF_U2 + (NSTG - 1) * NEQ)  // f(y) kept for a later stage whose argument is y itself
 #define OFF_C (OFF_F0 + NEQ)
 #else
-#define OFF_C (OFF_U2 + (RS - 1) * NEQ)
+#define OFF_C (OFF_U2 + (NSTG - 1) * NEQ)
 #endif
 #define OFF_CP (OFF_C + NS)
 #define OFF_HRT (OFF_CP + NS)

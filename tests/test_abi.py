@@ -44,9 +44,10 @@ def test_generated_kernels_compile_for_sm103a(tmp_path):
     assert "sm_103a" in log and "chem_integrate_k" in log
 
 
-@pytest.mark.parametrize("tableau", [1, 2, 3, 4])
+@pytest.mark.parametrize("tableau", [1, 2, 3, 4, 5])
 def test_every_method_compiles(tmp_path, tableau):
-    """ROS3, RODAS3, RODAS4 and the explicit RKF45 generate and compile (NVRTC, no GPU)."""
+    """ROS3, RODAS3, RODAS4, the explicit RKF45 and the W-method ROS2W generate and compile
+    (NVRTC, no GPU)."""
     from paper_2205_05681_gb300 import chem
     log = chem.compile_only(os.path.join(ROOT, "tests", "golden", "tiny_hon7.mech"), team=64,
                             block=64, cache_dir=str(tmp_path), tableau=tableau)

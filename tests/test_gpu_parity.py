@@ -661,7 +661,7 @@ def test_per_cell_method_switching(omech, gmech, name, team, block, alt):
     assert np.all(e[same] <= 1e-5), (e[same].max(), np.argmax(np.where(same, e, 0)))
     flips = np.where(~same)[0]
     # a flip can happen at every split step's decisions: at most 2% of the cells per split step
-    assert len(flips) <= max(1, int(0.02 * n * nsplit)), len(flips)
+    assert len(flips) <= max(1, int(np.ceil(0.02 * n * nsplit))), len(flips)
     if len(flips):
         yt, _ = _oracle_splits(om, y0[flips], st.P[flips], dt, nsplit, rtol=1e-10, atol=1e-14)
         assert np.all(weighted_norm(yt, yg[flips]) <= 10.0)
@@ -678,10 +678,10 @@ def test_w_method_with_factorisation_reuse(omech, gmech, name, team, block):
     from paper_2205_05681_gb300 import chem
     om = omech(name)
     g = gmech(name, team, block)
-    n = {"h2_13": 400, "ch4_53": 96, "ch4_111": 24}[name]
+    n = {"h2_13": 400, "ch4_53": 96, "ch4_111": 48}[name]
     nsplit, dt = 4, 1e-6
     st, y0 = _inputs(om, name, n, 161)
-    if name == "ch4_111":  # relaxed product cells: the regime where the factorisation is reused
+    if name != "h2_13":  # partly relaxed cells: the regime where the factorisation is reused
         yq, _ = om.integrate(y0, st.P, 1e-4, threads=16)
         st.T, st.Y = om.TY_from_state(yq)
         y0 = om.state_from_TY(st.T, st.Y)
@@ -712,7 +712,7 @@ def test_w_method_with_factorisation_reuse(omech, gmech, name, team, block):
     assert np.all(e[same] <= 1e-5), (e[same].max(), np.argmax(np.where(same, e, 0)))
     flips = np.where(~same)[0]
     # a flip can happen at every split step's decisions: at most 2% of the cells per split step
-    assert len(flips) <= max(1, int(0.02 * n * nsplit)), len(flips)
+    assert len(flips) <= max(1, int(np.ceil(0.02 * n * nsplit))), len(flips)
     if len(flips):
         yt, _ = _oracle_splits(om, y0[flips], st.P[flips], dt, nsplit, rtol=1e-10, atol=1e-14)
         assert np.all(weighted_norm(yt, yg[flips]) <= 10.0)
