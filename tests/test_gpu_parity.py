@@ -703,7 +703,9 @@ def test_w_method_with_factorisation_reuse(omech, gmech, name, team, block):
         assert (status.cpu().numpy() == 0).all() and np.all(info["status"] == 0)
         c = jc.view(n, stride).cpu().numpy()
         same &= att.cpu().numpy() == info["attempts"]
-        same &= (c[:, -1] == cache[2]) & (np.abs(c[:, -2] - cache[1]) <= 1e-12 * cache[1])
+        # the same reuse decisions: equal ages, and cache step sizes equal up to the drift of the
+        # step-size sequences (rounding; a different decision would store another step's size)
+        same &= (c[:, -1] == cache[2]) & (np.abs(c[:, -2] - cache[1]) <= 1e-6 * cache[1])
         if s > 0:
             reused += int((info["n_jac"] == 0).sum())
     assert reused > 0  # the cache was used across calls
