@@ -51,8 +51,8 @@ METHODS = ["ROS4", "ROS3", "RODAS3", "RODAS4", "RKF45", "ROS2W"]
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one chem_integrate_k launch on the
 # full bench workload, from a single-pass ncu capture; valid only for the device source they were
 # taken on (sha1 of csrc/ros4_device.cuh), reported as null once that source changes.
-MEASURED_TRAFFIC = {"device_src_sha1": "3eb154b40f5040d20298a37237fce177a1110511",
-                    "ch4_111_batched": 253508864 + 207848192}
+MEASURED_TRAFFIC = {"device_src_sha1": "126d9f93fe4d40e29e45844f7754caf7ad8a4e49",
+                    "ch4_111_batched": 252775168 + 208680960}
 
 
 def measured_traffic(wl, full_size):

@@ -1524,12 +1524,14 @@ __device__ __forceinline__ double shfl_xor(double a, int o) { return __shfl_xor_
 #define AOFF_UB (AOFF_YB + NEQ)
 #define AOFF_W (AOFF_UB + 4 * NEQ)
 #define AOFF_FB (AOFF_W + 4 * NEQ)
-#define AOFF_V (AOFF_FB + NEQ)
+#define AOFF_Y2 (AOFF_FB + NEQ)
+#define AOFF_Y3 (AOFF_Y2 + NEQ)
+#define AOFF_V (AOFF_Y3 + NEQ)
 #define AOFF_GP (AOFF_V + NEQ)
 #define AOFF_TMP (AOFF_GP + NR)
 #define AOFF_S (AOFF_TMP + NEQ)
 // S-typed (2 doubles each) scratch of the VJP: state, gy, C, hRT, cp, ex, iex, dcp, atilde, Cbar,
-// omega (11 x NS), plus 8 reduction slots
+// omega (11 x NS) and q (NR), plus 8 reduction slots
 #define VS_Y 0
 #define VS_GY (VS_Y + NEQ)
 #define VS_C (VS_GY + NEQ)
@@ -1541,7 +1543,8 @@ __device__ __forceinline__ double shfl_xor(double a, int o) { return __shfl_xor_
 #define VS_AT (VS_DCP + NS)
 #define VS_CB (VS_AT + NS)
 #define VS_OM (VS_CB + NS)
-#define VS_RED (VS_OM + NS)
+#define VS_Q (VS_OM + NS)
+#define VS_RED (VS_Q + NR)
 #define VS_TOTAL (VS_RED + 8 * TEAM / 32)
 #define ASLOTS (AOFF_S + 2 * VS_TOTAL)
 
@@ -1606,7 +1609,6 @@ __device__ void vjp(const Team& tm, double P, const double* __restrict__ lnA_ext
     sb[VS_IEX + k] = 1.0 / ex;
     sb[VS_DCP + k] = dcp;
     sb[VS_CB + k] = Z;
-    sb[VS_OM + k] = Z;
     cpm = cpm + n * cp;
     dcpm = dcpm + n * dcp;
   }
@@ -1696,9 +1698,7 @@ __device__ void vjp(const Team& tm, double P, const double* __restrict__ lnA_ext
     const S m = kind == THIRD ? M : Z + 1.0;
     const S qnet = fwd - rev;
     const S q = m * qnet;
-    // omega = sum_r nu_kr q_r, scattered (the per-reaction q would cost NR slots of shared memory)
-    for (int i = 0; i < nre; ++i) atomic_add_s(&sb[VS_OM + mk_rsp[r][i]], -(mk_rnuf[r][i] * q));
-    for (int i = 0; i < npr; ++i) atomic_add_s(&sb[VS_OM + mk_psp[r][i]], mk_pnuf[r][i] * q);
+    sb[VS_Q + r] = q;
     // parameter: d q / d lnA_r = q (d ln kf / d ln k_inf)
     const S gpr = abar * q * one_minus_g;
     gp[r] += S_is_dual<S>::value ? dof(gpr) : vof(gpr);
@@ -1734,10 +1734,13 @@ __device__ void vjp(const Team& tm, double P, const double* __restrict__ lnA_ext
   Tbar = team_sum_s(tm, Tbar, red);
   Bbar = team_sum_s(tm, Bbar, red);
   tsync();
-  // the mixture sums that use omega
+  // omega from q (fixed-order gather), and the mixture sums that use it
   S Q = Z, cpw = Z, vw = Z, Dbar = Z;
   for (int k = tm.tl; k < NS; k += TEAM) {
-    const S om = sb[VS_OM + k];
+    S om = Z;
+    for (int sg = mk_spseg_beg[k]; sg < mk_spseg_beg[k + 1]; ++sg)
+      for (int e = mk_gseg_beg[sg]; e < mk_gseg_beg[sg + 1]; ++e) om = om + mk_gent_nu[e] * sb[VS_Q + mk_gent_rx[e]];
+    sb[VS_OM + k] = om;
     Q = Q + sb[VS_HRT + k] * om;
     cpw = cpw + sb[VS_CP + k] * om;
     if (k < NS - 1) vw = vw + v[1 + k] * om;
@@ -1804,17 +1807,6 @@ __device__ __forceinline__ void set_vjp_state(const Team& tm, int oy, int odir) 
   tsync();
 }
 
-// VJP state at a stage argument, recomputed from y (OFF_Y), u1 and u2 as the forward formed it:
-// Y2 = y + a21 u1 (ST == 1), Y3 = y + a31 u1 + a32 u2 (ST == 2)
-template <int ST>
-__device__ __forceinline__ void set_vjp_stage(const Team& tm) {
-  double* sb = &tm.base[AOFF_S];
-  for (int i = tm.tl; i < NEQ; i += TEAM)
-    sb[VS_Y + i] = ST == 1 ? tm.at(OFF_Y, i) + RA21 * tm.at(OFF_U1, i)
-                           : tm.at(OFF_Y, i) + RA31 * tm.at(OFF_U1, i) + RA32 * tm.at(OFF_U2, i);
-  tsync();
-}
-
 __device__ __forceinline__ void add_gy(const Team& tm, bool dual, int o1, double c1, int o2, double c2, int o3, double c3) {
   for (int i = tm.tl; i < NEQ; i += TEAM) {
     double g;
@@ -1845,14 +1837,21 @@ __device__ void adjoint_step(const Team& tm, double P, double h, const double* l
   eval_f_jac(tm, OFF_Y, U1, P, lnA_ext, -1.0, 1.0 / (RGAM * h));
   lu_factor(tm);
   lu_solve_col(tm, U1);
-  for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(OFF_YT, i) = tm.at(OFF_Y, i) + RA21 * tm.at(U1, i);
+  for (int i = tm.tl; i < NEQ; i += TEAM) {
+    const double v = tm.at(OFF_Y, i) + RA21 * tm.at(U1, i);
+    tm.at(OFF_YT, i) = v;
+    tm.at(AOFF_Y2, i) = v;
+  }
   tsync();
   eval_f(tm, OFF_YT, OFF_F, P, lnA_ext);
   for (int i = tm.tl; i < NEQ; i += TEAM) tm.at(U2, i) = tm.at(OFF_F, i) + (RC21 * ih) * tm.at(U1, i);
   tsync();
   lu_solve_col(tm, U2);
-  for (int i = tm.tl; i < NEQ; i += TEAM)
-    tm.at(OFF_YT, i) = tm.at(OFF_Y, i) + RA31 * tm.at(U1, i) + RA32 * tm.at(U2, i);
+  for (int i = tm.tl; i < NEQ; i += TEAM) {
+    const double v = tm.at(OFF_Y, i) + RA31 * tm.at(U1, i) + RA32 * tm.at(U2, i);
+    tm.at(OFF_YT, i) = v;
+    tm.at(AOFF_Y3, i) = v;
+  }
   tsync();
   eval_f(tm, OFF_YT, OFF_F, P, lnA_ext);
   for (int i = tm.tl; i < NEQ; i += TEAM)
@@ -1898,7 +1897,7 @@ __device__ void adjoint_step(const Team& tm, double P, double h, const double* l
     tm.at(B2, i) += (RC32 * ih) * w;
   }
   tsync();
-  set_vjp_stage<2>(tm);  // Y3
+  set_vjp_state<double>(tm, AOFF_Y3, AOFF_Y3);
   vjp<double>(tm, P, lnA_ext);
   add_gy(tm, false, AOFF_YB, 1.0, B1, RA31, B2, RA32);
   // stage 2
@@ -1911,7 +1910,7 @@ __device__ void adjoint_step(const Team& tm, double P, double h, const double* l
     tm.at(B1, i) += (RC21 * ih) * w;
   }
   tsync();
-  set_vjp_stage<1>(tm);  // Y2
+  set_vjp_state<double>(tm, AOFF_Y2, AOFF_Y2);
   vjp<double>(tm, P, lnA_ext);
   add_gy(tm, false, AOFF_YB, 1.0, B1, RA21, -1, 0.0);
   // stage 1
@@ -1948,10 +1947,9 @@ __device__ __forceinline__ long long team_global_id() {
 // accepted steps are recomputed from their checkpoint (states kept in this team's slice of
 // `seg`), then stepped through backwards.  dL/dlnA is accumulated per team and written to
 // gp_partial[team][r]; chem_adjoint_reduce_k sums the teams in a fixed order.
-// (register bound: five 64-lane teams per SM, the most the adjoint's shared memory allows at 53
-// species; one 256-lane team otherwise, so that the registers go to avoiding spills)
-#define ADJ_MIN_BLOCKS (TEAM == 64 ? 5 : 1)
-extern "C" __global__ void __launch_bounds__(TPB, ADJ_MIN_BLOCKS)
+// (one block per SM as the register bound: the adjoint's shared memory already limits residency
+// to four 64-lane or one 256-lane team per SM, so the registers go to avoiding spills)
+extern "C" __global__ void __launch_bounds__(TPB, 1)
 chem_adjoint_k(long long n_cells, const double* __restrict__ P, const double* __restrict__ gT,
                const double* __restrict__ gY, long long ld, double* __restrict__ gT0,
                double* __restrict__ gY0, const double* __restrict__ lnA_ext,
