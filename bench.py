@@ -51,8 +51,8 @@ METHODS = ["ROS4", "ROS3", "RODAS3", "RODAS4", "RKF45", "ROS2W"]
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one chem_integrate_k launch on the
 # full bench workload, from a single-pass ncu capture; valid only for the device source they were
 # taken on (sha1 of csrc/ros4_device.cuh), reported as null once that source changes.
-MEASURED_TRAFFIC = {"device_src_sha1": "126d9f93fe4d40e29e45844f7754caf7ad8a4e49",
-                    "ch4_111_batched": 252775168 + 208680960}
+MEASURED_TRAFFIC = {"device_src_sha1": "f1b905e47ed9e78a139baa637f5a494d9b1355b6",
+                    "ch4_111_batched": 252589568 + 207334656}
 
 
 def measured_traffic(wl, full_size):
@@ -887,6 +887,14 @@ def main():
     clk = run["clocks"]
     rl = roofline(spec, args.tableau, float(attempts.sum()), sec, probe, dgemm, clk.get("sm_mhz"),
                   props.multi_processor_count, wl, full, n_cells, splits)
+    if args.switching:
+        # the attempts mix two methods (an attempt of the alternative is not a Rosenbrock attempt)
+        # and the integrator launches cover subsets of the cells: no flop rate or traffic applies
+        for k in ("achieved", "frac", "frac_vs_dgemm", "achieved_with_transcendentals",
+                  "frac_with_transcendentals", "traffic", "traffic_source"):
+            rl[k] = None
+        rl["note"] = ("per-cell switching: attempts of two methods, no flop rate derived; the "
+                      "single-method run carries the roofline")
     if "forward_53" in extra:
         f53 = extra["forward_53"]
         r53 = roofline(f53.pop("_spec"), 0, float(f53["attempts"]["total"]), f53.pop("_sec"),

@@ -132,8 +132,9 @@ typedef struct {
                           (an all-zero cache is empty); keep it with the cells between calls. */
   int32_t alt_tableau;  /* the alternative method of cell_method switching: 0 or CHEM_RKF45 (the
                           stiffness rule above), or CHEM_ROS2W (needs jac_cache): a cell whose
-                          Rosenbrock integration took a single attempt (quiescent, e.g. near
-                          equilibrium) runs the W-method on the next call with budget 12, reusing
+                          Rosenbrock integration took a single attempt and left a next-step
+                          proposal h of at least 2 dt (quiescent, e.g. near equilibrium) runs
+                          the W-method on the next call with budget 12, reusing
                           its cached factorisation across calls; the Rosenbrock launch empties the
                           cache of the cells it integrates. */
 } chem_int_opts;

@@ -1035,8 +1035,10 @@ int orc_integrate(void* hm, int n, double* y, const double* P, const double* lnA
 // outnumber the Rosenbrock attempts).  Cells below T_min or with a non-finite state keep their
 // method.  attempts and status are those of the run that finished the cell.
 // alt = 5 takes the W-method (with the caches Wc, hW, age of orc_integrate_w) as the alternative:
-// a cell goes to it after a single-attempt Rosenbrock integration (budget 12), and every
-// Rosenbrock integration empties the cell's cache.
+// a cell goes to it (budget 12) after a Rosenbrock integration of one attempt whose next-step
+// proposal h_out is at least 2 dt (quiescent: a cell whose single step only just fitted would
+// need many steps of the second-order W-method), and every Rosenbrock integration empties the
+// cell's cache.
 int orc_integrate_auto(void* hm, int n, double* y, const double* P, const double* lnA, double dt, double rtol,
                        double atol, double* h, int* status, int* attempts, int* method, int max_steps,
                        double T_min, int nthreads, int tab, int alt, double* Wc, double* hW, int* wage) {
@@ -1089,7 +1091,7 @@ int orc_integrate_auto(void* hm, int n, double* y, const double* P, const double
         o.rtol = rtol; o.atol = atol; o.max_steps = max_steps;
         r = integrate_one(sys, tr, yc, dt, h_in, o, nullptr);
         if (alt == 5) {
-          method[c] = (r.status == OK && r.attempts == 1) ? 12 : 0;
+          method[c] = (r.status == OK && r.attempts == 1 && r.h_out >= 2.0 * dt) ? 12 : 0;
           hW[c] = 0.0;
         } else {
           method[c] = (r.status == OK && dt * rho <= 3.0 * r.attempts) ? 4 * r.attempts + 8 : 0;

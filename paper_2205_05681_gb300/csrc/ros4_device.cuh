@@ -1171,8 +1171,10 @@ chem_eval_jacobian_k(long long n_cells, const double* __restrict__ T, const doub
 //   * alternative RKF45 (AUTO_IMPLICIT): when dt * rho <= STIFF_BETA * attempts, rho the stiffness
 //     estimate at the cell's first attempt (the explicit method's stability-limited steps, about
 //     dt * rho / STIFF_BETA, would not outnumber the Rosenbrock attempts);
-//   * alternative W-method (AUTO_IMPLICIT_W): when the cell took a single attempt (a quiescent
-//     cell, whose split steps the cached factorisation can serve); its cache is emptied, so the
+//   * alternative W-method (AUTO_IMPLICIT_W): when the cell took a single attempt and the
+//     controller's next-step proposal is at least W_ENTRY_MARGIN * dt (a quiescent cell, whose
+//     split steps the cached factorisation can serve; a cell whose one step only just fitted
+//     would need many more steps of the second-order W-method); its cache is emptied, so the
 //     W-method starts from a Jacobian at its own state;
 // with budget 4 * attempts + 8; after a success of the alternative method with a attempts, it
 // stays with budget 4a + 8.
@@ -1180,6 +1182,7 @@ chem_eval_jacobian_k(long long n_cells, const double* __restrict__ T, const doub
 #define AUTO_IMPLICIT 2
 #define AUTO_IMPLICIT_W 3
 #define STIFF_BETA 3.0
+#define W_ENTRY_MARGIN 2.0
 
 // Persistent driver: each team pulls cells from the queue counter and integrates them to dt.
 // With TEAM == 1 each thread refills independently (per-lane refill of retired cells); the
@@ -1292,7 +1295,8 @@ chem_integrate_k(long long n_cells, double* __restrict__ T, const double* __rest
           cell_method[cell] = (c.status == ST_OK && dt * c.rho <= STIFF_BETA * c.attempts)
                                   ? 4 * c.attempts + 8 : 0;
         else if (auto_mode == AUTO_IMPLICIT_W) {  // the W-method next time if quiescent
-          cell_method[cell] = (c.status == ST_OK && c.attempts == 1) ? 12 : 0;
+          cell_method[cell] =
+              (c.status == ST_OK && c.attempts == 1 && c.h >= W_ENTRY_MARGIN * dt) ? 12 : 0;
           if (jac_cache) jac_cache[cell * (long long)WC_STRIDE + WC_H] = 0.0;
         }
       }

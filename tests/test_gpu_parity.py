@@ -650,8 +650,8 @@ def test_per_cell_method_switching(omech, gmech, name, team, block, alt):
         same &= (mg == mo) & (att.cpu().numpy() == info["attempts"])
         # the method chosen for the next split step (its budget follows the attempt count)
         assert ((mg > 0) != (mo > 0)).mean() <= 0.02, (s, ((mg > 0) != (mo > 0)).sum())
-    if alt == 5:
-        assert (mo > 0).mean() > 0.3  # quiescent cells move to the W-method
+    if alt == 5:  # quiescent cells move to the W-method (the partly reacted H2 cells: some)
+        assert (mo > 0).mean() > (0.15 if name == "h2_13" else 0.5)
     elif name == "h2_13":
         assert (mo > 0).mean() > 0.5  # most of these cells run explicitly after the first step
     else:

@@ -88,7 +88,8 @@ def test_w_method_alternative_for_quiescent_cells(omech):
     assert np.all(cache[1] == 0.0)  # emptied by the Rosenbrock integration
     yr, ir = om.integrate(y, st.P, 1e-6, threads=1)
     assert np.array_equal(y1, yr)
-    assert np.array_equal(meth, np.where(ir["attempts"] == 1, 12, 0).astype(np.int32))
+    quiescent = (ir["attempts"] == 1) & (ir["h"] >= 2e-6)
+    assert np.array_equal(meth, np.where(quiescent, 12, 0).astype(np.int32))
     assert np.all(meth[:4] == 12)
     y2, i2 = om.integrate_auto(y1, st.P, 1e-6, meth, h=i1["h"], alt=O.ROS2W, cache=cache)
     assert np.all(i2["status"] == 0)
@@ -97,3 +98,22 @@ def test_w_method_alternative_for_quiescent_cells(omech):
     y3, i3 = om.integrate_auto(y2, st.P, 1e-6, meth, h=i2["h"], alt=O.ROS2W, cache=cache)
     quiet = i3["attempts"][:4] == 1
     assert quiet.any() and np.all(cache[2][:4][quiet] == age[quiet] + 1)  # reused, aged by one
+
+
+def test_w_method_entry_needs_a_step_margin(omech):
+    """A single-attempt Rosenbrock split step sends a cell to the W-method only when the step-size
+    controller proposes at least 2 dt next: four cells relaxed for 1e-4 s, one step of 2e-4 s each,
+    two with a proposal below the margin (the one step only just fitted) and two above."""
+    om = omech("h2_13")
+    st = states("h2_13", 8, "h2_fresh", 405)
+    P = st.P[:4]
+    yq, _ = om.integrate(om.state_from_TY(st.T[:4], st.Y[:4]), P, 1e-4)
+    dt = 2e-4
+    yr, ir = om.integrate(yq, P, dt, threads=1)
+    assert np.all(ir["attempts"] == 1)
+    below = ir["h"] < 2 * dt
+    assert below.any() and not below.all()  # both branches of the rule
+    meth = np.zeros(4, dtype=np.int32)
+    y, info = om.integrate_auto(yq, P, dt, meth, alt=O.ROS2W, cache=om.w_cache(4))
+    assert np.array_equal(y, yr)
+    assert np.array_equal(meth, np.where(below, 0, 12).astype(np.int32))
