@@ -640,6 +640,47 @@ __device__ void eval_f_jac(const Team& tm, int oy, int of, double P, const doubl
 
 // ------------------------------------------------------------------------------ LU + solves
 
+#if TEAM >= 128
+// Look-ahead part of the multi-warp LU, run by the team's first warp: column c (rows c..N-1)
+// receives the rank-1 update of step c-1 (c > 0), then its pivot (largest |a|, lowest row on
+// ties) and the pivot's inverse go to the team's scratch slots LU_PIV / LU_INV.
+#define LU_INV (OFF_RED + 21)
+#define LU_PIV (OFF_RED + 22)
+__device__ __forceinline__ void lu_panel(const Team& tm, int c) {
+  long long best = -1;
+  int p = NEQ;
+  const double u = c > 0 ? tm.A(c - 1, c) : 0.0;
+  for (int i = c + tm.tl; i < NEQ; i += 32) {
+    double a = tm.A(i, c);
+    if (c > 0) {
+      a = fma(-tm.A(i, c - 1), u, a);
+      tm.A(i, c) = a;
+    }
+    const long long v = abs_key(a);
+    if (v > best) { best = v; p = i; }
+  }
+  {
+    // warp argmax in three reductions: the high word of the key, the low word among the lanes
+    // holding that maximum, the lowest row among the lanes holding both (a lane without rows
+    // enters key 0 with row NEQ and so never wins over a row of the column)
+    const unsigned long long key = best < 0 ? 0ULL : (unsigned long long)best;
+    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+    const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+    p = (int)__reduce_min_sync(0xffffffffu, (hi == mhi && lo == mlo) ? (unsigned)p : 0xffffffffu);
+  }
+  __syncwarp();  // the updated column is visible to the whole warp
+  const double inv = 1.0 / tm.A(p, c);
+  if (tm.tl == 0) {
+    tm.base[LU_INV] = inv;
+    reinterpret_cast<int*>(&tm.base[LU_PIV])[0] = p;
+  }
+}
+// elements of a rank-1 update that each lane of the first warp leaves to the other warps, in
+// exchange for the look-ahead column it handles
+#define LU_PANEL_SHARE 8
+#endif
+
 // In-place LU with partial pivoting of A (N x N): largest |a| in the column, lowest row on
 // ties.  1/U_kk replaces U_kk on the diagonal, the composed row permutation (row i of P A is row
 // perm[i] of A) goes to OFF_PERM, and the single-lane layout also keeps the pivot sequence.
@@ -665,6 +706,70 @@ __device__ void lu_factor(const Team& tm) {
   }
   for (int i = 0; i < NEQ; ++i) tm.perm(i) = i;
   for (int k = 0; k < NEQ; ++k) { const int p = tm.piv(k); if (p != k) { const int t = tm.perm(k); tm.perm(k) = tm.perm(p); tm.perm(p) = t; } }
+#elif TEAM >= 128
+  // Right-looking elimination with one column of look-ahead: while the team applies step k's
+  // rank-1 update to columns k+2.., the first warp updates column k+1 and finds its pivot and the
+  // pivot's inverse (lu_panel), so that the search, its reduction and the division stay off the
+  // barrier-separated critical path: two barriers per column.  Every element receives the same
+  // operations in the same order as in the column-by-column form.
+  for (int i = tm.tl; i < NEQ; i += TEAM) tm.perm(i) = i;
+  if (tm.tl < 32) lu_panel(tm, 0);
+  tsync();
+  for (int k = 0; k < NEQ; ++k) {
+    const int p = reinterpret_cast<const int*>(&tm.base[LU_PIV])[0];
+    const double inv = tm.base[LU_INV];
+    // rows k and p exchanged (every column but k), column k below the diagonal scaled by the
+    // pivot's inverse, which replaces U_kk; the lane of row p also moves U_kk's old value
+    if (p != k)
+      for (int j = tm.tl; j < NEQ; j += TEAM)
+        if (j != k) { const double t = tm.A(k, j); tm.A(k, j) = tm.A(p, j); tm.A(p, j) = t; }
+    for (int i = k + 1 + tm.tl; i < NEQ; i += TEAM) {
+      if (i == p) {
+        const double t = tm.A(k, k);
+        tm.A(k, k) = inv;
+        tm.A(p, k) = t * inv;
+      } else {
+        tm.A(i, k) *= inv;
+      }
+    }
+    if (tm.tl == 0) {
+      if (p == k) {
+        tm.A(k, k) = inv;
+      } else {
+        const int t = tm.perm(k);
+        tm.perm(k) = tm.perm(p);
+        tm.perm(p) = t;
+      }
+    }
+    tsync();
+    const int m = NEQ - k - 1;
+    if (m > 0) {
+      if (tm.tl < 32) lu_panel(tm, k + 1);
+      // rank-1 update of rows k+1.., columns k+2.. (m x n2 elements in row-major order): the
+      // first warp's lanes take the first e0 of them, LU_PANEL_SHARE fewer each than the others
+      const int n2 = m - 1;
+      if (n2 > 0) {
+        const int tot = m * n2;
+        int e0 = (tot - LU_PANEL_SHARE * (TEAM - 32)) * 32 / TEAM;
+        e0 = e0 > 0 ? e0 : 0;
+        int e, st, end;
+        if (tm.tl < 32) { e = tm.tl; st = 32; end = e0; }
+        else { e = e0 + tm.tl - 32; st = TEAM - 32; end = tot; }
+        if (e < end) {
+          int i = e / n2, j = e - (e / n2) * n2;
+          const int qd = st / n2, rm = st - qd * n2;
+          for (; e < end; e += st) {
+            double& a = tm.A(k + 1 + i, k + 2 + j);
+            a = fma(-tm.A(k + 1 + i, k), tm.A(k, k + 2 + j), a);
+            i += qd;
+            j += rm;
+            if (j >= n2) { j -= n2; ++i; }
+          }
+        }
+      }
+      tsync();
+    }
+  }
 #else
   // the composed permutation is built as the pivots are chosen (lane 0, after the row swap's
   // barrier), so no serial pass over the pivots is needed afterwards
@@ -729,7 +834,15 @@ __device__ void lu_factor(const Team& tm) {
 #endif
 }
 
-// Solve (LU) x = b in place on the vector at slot ob.  With TEAM > 1 only the first warp works.
+#if TEAM >= 128 && NB >= 2 && NB <= TEAM / 32
+// barrier of the solve's NB warps (barrier 0 is the team's)
+__device__ __forceinline__ void solve_bar() {
+  asm volatile("bar.sync 1, %0;" ::"r"(NB * 32) : "memory");
+}
+#endif
+
+// Solve (LU) x = b in place on the vector at slot ob.  With TEAM > 1 only the first warp works,
+// except for teams of four or more warps, where warp w holds rows 32w..32w+31.
 __device__ void lu_solve(const Team& tm, int ob) {
 #if TEAM == 1
   for (int k = 0; k < NEQ; ++k) {
@@ -746,6 +859,69 @@ __device__ void lu_solve(const Team& tm, int ob) {
     for (int j = i + 1; j < NEQ; ++j) s -= tm.A(i, j) * tm.at(ob, j);
     tm.at(ob, i) = s * tm.invd(i);
   }
+#elif TEAM >= 128 && NB >= 2 && NB <= TEAM / 32
+  // Blocked substitution over NB warps, one 32-row block each, so that the FP64 work is spread
+  // over the SM's sub-partitions instead of one: warp b solves its diagonal block (the finished
+  // x_k broadcast by a shuffle, as below), publishes the block's values in the vector's slot, and
+  // after a barrier of the NB warps the others apply the block's columns to their rows.  Every
+  // row receives its updates in the same order (k increasing forward, decreasing backward) and
+  // with the same operations as in the single-warp form.
+  const int w = tm.tl >> 5, ln = tm.tl & 31;
+  if (w < NB) {
+    const int i = w * 32 + ln;
+    double xr = i < NEQ ? tm.at(ob, tm.perm(i)) : 0.0;  // P b
+    solve_bar();  // every entry of b is read before the slot receives x
+    // L (unit lower) forward
+    for (int b = 0; b < NB; ++b) {
+      if (w == b) {
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) {
+          const int k = b * 32 + kk;
+          if (k < NEQ - 1) {
+            const double xk = __shfl_sync(0xffffffffu, xr, kk);
+            if (ln > kk && i < NEQ) xr = fma(-tm.A(i, k), xk, xr);
+          }
+        }
+        if (i < NEQ) tm.at(ob, i) = xr;
+      }
+      if (b + 1 < NB) {
+        solve_bar();
+        if (w > b && i < NEQ) {
+#pragma unroll 8
+          for (int kk = 0; kk < 32; ++kk) {
+            const int k = b * 32 + kk;
+            xr = fma(-tm.A(i, k), tm.at(ob, k), xr);
+          }
+        }
+      }
+    }
+    // U backward, 1/U_kk from the factorisation
+    for (int b = NB - 1; b >= 0; --b) {
+      if (w == b) {
+#pragma unroll
+        for (int kk = 31; kk >= 0; --kk) {
+          const int k = b * 32 + kk;
+          if (k < NEQ) {
+            const double xk = __shfl_sync(0xffffffffu, xr, kk) * tm.invd(k);
+            if (ln == kk) xr = xk;
+            if (ln < kk) xr = fma(-tm.A(i, k), xk, xr);
+          }
+        }
+        if (i < NEQ) tm.at(ob, i) = xr;
+      }
+      if (b > 0) {
+        solve_bar();
+        if (w < b) {
+#pragma unroll 8
+          for (int kk = 31; kk >= 0; --kk) {
+            const int k = b * 32 + kk;
+            if (k < NEQ) xr = fma(-tm.A(i, k), tm.at(ob, k), xr);
+          }
+        }
+      }
+    }
+  }
+  tsync();
 #else
   // One warp, the vector in registers: lane l holds rows l, l + 32, ... (NB chunks).  Each
   // substitution step broadcasts the finished x_k with a shuffle and updates the rows it feeds,
