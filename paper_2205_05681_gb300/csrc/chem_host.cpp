@@ -384,9 +384,12 @@ void emit_array(std::ostringstream& o, const char* type, const char* name, const
 
 // Kernel order of the reactions: grouped by the branches the reaction code takes (kind, Troe
 // T** term, third-body efficiency count, reactant and product counts and coefficients), stable
-// within a group.  Lanes of a warp take consecutive reactions, so grouped reactions keep the
-// warp on one path; mechanisms that interleave falloff and plain reactions would otherwise pay
-// the falloff branch in almost every warp.  Returns order[kernel index] = mechanism index.
+// within a group, the costliest groups first.  Lanes of a warp take consecutive reactions, so
+// grouped reactions keep the warp on one path (mechanisms that interleave falloff and plain
+// reactions would otherwise pay the falloff branch in almost every warp), and with the falloff
+// groups first they fill whole warps while the last, partly filled round of the team's loop
+// takes elementary reactions: a warp instruction costs its FP64 pipe time whatever the number of
+// its active lanes.  Returns order[kernel index] = mechanism index.
 std::vector<int> kernel_reaction_order(const MechData& m) {
   std::vector<int> order(m.rx.size());
   for (size_t r = 0; r < order.size(); ++r) order[r] = (int)r;
@@ -400,7 +403,7 @@ std::vector<int> kernel_reaction_order(const MechData& m) {
     for (int i = 0; i < x.npr; ++i) k.push_back(x.pnu[i]);
     return k;
   };
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(b) < key(a); });
   return order;
 }
 
