@@ -51,8 +51,8 @@ METHODS = ["ROS4", "ROS3", "RODAS3", "RODAS4", "RKF45", "ROS2W"]
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one chem_integrate_k launch on the
 # full bench workload, from a single-pass ncu capture; valid only for the device source they were
 # taken on (sha1 of csrc/ros4_device.cuh), reported as null once that source changes.
-MEASURED_TRAFFIC = {"device_src_sha1": "f1b905e47ed9e78a139baa637f5a494d9b1355b6",
-                    "ch4_111_batched": 252589568 + 207334656}
+MEASURED_TRAFFIC = {"device_src_sha1": "4ff7f10b7da918bc04f1b55c6db25a30a4a18cc9",
+                    "ch4_111_batched": 250775808 + 204967680}
 
 
 def measured_traffic(wl, full_size):
